@@ -1,0 +1,115 @@
+"""Pins of the oracle's lattice tables, equilibrium and small closed forms.
+
+Each check is a property the mathematics fixes independently of how the oracle
+is written: lattice isotropy (the moment identities that make the discrete
+velocity set reproduce Navier-Stokes), the closed-form moments of the
+second-order equilibrium, the Smagorinsky defining equation, library rounding
+routines, and the performance-model figures printed in Sec. 4.1.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+
+KD = np.eye(3)
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_lattice_isotropy(Q):
+    c, w, opp = oracle.lattice(Q)
+    assert len({tuple(v) for v in c}) == Q
+    assert np.all(np.abs(c) <= 1)
+    if Q == 19:
+        assert np.all(np.sum(c * c, axis=1) <= 2)
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.allclose(np.einsum("i,ia->a", w, c), 0.0, atol=1e-16)
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, c, c), KD / 3.0, atol=1e-16)
+    assert np.allclose(np.einsum("i,ia,ib,ic->abc", w, c, c, c), 0.0, atol=1e-16)
+    m4 = np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c)
+    iso = (np.einsum("ab,cd->abcd", KD, KD) + np.einsum("ac,bd->abcd", KD, KD)
+           + np.einsum("ad,bc->abcd", KD, KD)) / 9.0
+    assert np.allclose(m4, iso, atol=1e-16)
+    # opposites: an involution pairing c with -c, stored as adjacent pairs
+    assert np.all(opp[opp] == np.arange(Q))
+    assert np.all(c[opp] == -c)
+    assert opp[0] == 0
+    for i in range(1, Q, 2):
+        assert opp[i] == i + 1
+
+
+def test_d3q27_is_full_cube():
+    c, _, _ = oracle.lattice(27)
+    assert {tuple(v) for v in c} == set(itertools.product((-1, 0, 1), repeat=3))
+
+
+def test_bad_lattice_rejected():
+    with pytest.raises(ValueError):
+        oracle.lattice(15)
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_equilibrium_moments(Q):
+    c, _, _ = oracle.lattice(Q)
+    rng = np.random.default_rng(7)
+    for _ in range(50):
+        rho = rng.uniform(0.5, 1.5)
+        u = rng.uniform(-0.2, 0.2, size=3)
+        feq = oracle.equilibrium(Q, rho, u)
+        assert abs(feq.sum() - rho) < 1e-14
+        assert np.allclose(np.einsum("i,ia->a", feq, c), rho * u, atol=1e-15)
+        pi = np.einsum("i,ia,ib->ab", feq, c, c)
+        assert np.allclose(pi, rho * np.outer(u, u) + rho / 3.0 * KD, atol=1e-14)
+
+
+def test_smagorinsky_defining_equation():
+    """tau_eff = tau0 + 3 nu_t with nu_t = Cs^2 |S|, |S| = sqrt(2 S:S) and
+    S = -Pi / (2 rho c_s^2 tau_eff): the closed form must satisfy it."""
+    rng = np.random.default_rng(3)
+    for _ in range(100):
+        tau0 = rng.uniform(0.501, 1.5)
+        cs = rng.uniform(0.05, 0.3)
+        rho = rng.uniform(0.8, 1.2)
+        pi6 = rng.normal(scale=1e-3, size=6)
+        te = oracle.tau_smagorinsky(tau0, cs, rho, pi6)
+        P = np.array([[pi6[0], pi6[3], pi6[4]], [pi6[3], pi6[1], pi6[5]], [pi6[4], pi6[5], pi6[2]]])
+        S = -P / (2.0 * rho * (1.0 / 3.0) * te)
+        Smag = np.sqrt(2.0 * np.sum(S * S))
+        assert te == pytest.approx(tau0 + 3.0 * cs * cs * Smag, rel=1e-13)
+        assert te >= tau0
+    assert oracle.tau_smagorinsky(0.6, 0.0, 1.0, np.ones(6)) == 0.6
+
+
+def test_storage_rounding_matches_library_routines():
+    rng = np.random.default_rng(11)
+    h = np.concatenate([rng.normal(scale=s, size=2000) for s in (1e-1, 1e-3, 1e-5, 1e-7)])
+    f16 = np.float16(np.float32(h)).astype(np.float64)
+    bf = torch.tensor(np.float32(h)).to(torch.bfloat16).to(torch.float64).numpy()
+    f32 = np.float32(h).astype(np.float64)
+    for k in range(len(h)):
+        assert oracle.round_scalar(h[k], oracle.F16) == f16[k]
+        assert oracle.round_scalar(h[k], oracle.BF16) == bf[k]
+        assert oracle.round_scalar(h[k], oracle.F32) == f32[k]
+        assert oracle.round_scalar(h[k], oracle.F64) == h[k]
+
+
+def test_round_storage_keeps_offset():
+    c, w, _ = oracle.lattice(19)
+    f = w[:, None] * (1.0 + np.linspace(-0.1, 0.1, 7)[None, :])
+    g = oracle.round_storage(f, oracle.BF16)
+    for i in range(19):
+        for n in range(7):
+            assert g[i, n] == w[i] + oracle.round_scalar(f[i, n] - w[i], oracle.BF16)
+
+
+def test_performance_model_reproduces_paper():
+    """Sec. 4.1: 1.555 TB/s over n_t = 2*19*n_store + 12 bytes gives 9.481 and
+    4.921 GLUPS; the memory-use model (read as n_t L^3 / 40 GB) gives about
+    51% and 99% at L = 500."""
+    assert abs(oracle.glups_peak(1.555e12, 19, 4) - 9.481) < 1e-3
+    assert abs(oracle.glups_peak(1.555e12, 19, 8) - 4.921) < 1e-3
+    for n_store, pct in ((4, 51), (8, 99)):
+        mem = (2 * 19 * n_store + 12) * 500 ** 3 / 40e9
+        assert round(100 * mem) == pct
