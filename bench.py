@@ -1,0 +1,434 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 lattice Boltzmann hot path.
+
+Metric: GLUPS (10^9 lattice-node updates per second) of the fused
+collide-and-stream step, next to the HBM roofline of its algorithmic traffic
+(2 Q s bytes per node update: every population read once and written once).
+
+Default workload: periodic 3D Taylor-Green vortex, 512^3 nodes, D3Q19, FP32
+populations, Re = 1600, u0 = 0.04 (tau = 0.506112), BGK.  One benchmark step
+is ``inner`` lattice steps followed by the FP64 reduction (mass, momentum,
+kinetic energy) read back to the host, as a run that samples its kinetic
+energy does.  Inputs (two population arrays of 10.2 GB each) are far larger
+than L2, so no flush is needed between steps.
+
+Also reported: ``e2e`` (each step uploads the initial fields from pinned host
+memory through the C ABI, runs the lattice steps and reads the reduction
+back), FP16/BF16-shifted and other workload variants with their error against
+the FP64 run, SM clocks sampled during the timed region, and the CPU oracle
+timed on the host cores.
+
+Launch: ``python bench.py [--gpus N --steps K --warmup W]``; for N > 1 under
+torchrun every rank runs an independent replica (the path has no exchange
+step on one lattice per GPU), timing is the max over ranks, and the value is
+the sum over ranks.  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+if str(ROOT) not in sys.path:
+    sys.path.insert(0, str(ROOT))
+
+METRIC = "GLUPS per GB300 vs HBM roofline; FP32 vs FP16-shifted storage at stated error"
+UNIT = "GLUPS"
+SIZE = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+
+
+# ---------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------
+def tgv_tau(n: int, u0: float, re: float) -> float:
+    """tau for a Taylor-Green vortex whose reference length is n / (2 pi)."""
+    return 0.5 + 3.0 * u0 * (n / (2.0 * math.pi)) / re
+
+
+_FIELDS = {}
+
+
+def tgv_fields(n: int):
+    """The 3D Taylor-Green initial fields, generated once per size."""
+    import lbm_inputs as inp
+    if n not in _FIELDS:
+        _FIELDS.clear()
+        _FIELDS[n] = inp.tgv3d(n, 0.04)
+    return _FIELDS[n]
+
+
+def make_workload(name: str, dtype: str):
+    """Returns (lattice, fields, description) with the lattice initialised."""
+    import lbm_inputs as inp
+    from paper_2506_09242_gb300 import lbm
+
+    m = re.fullmatch(r"(tgv|cavity)(\d+)_d3q(19|27)", name)
+    if not m:
+        raise SystemExit(f"unknown workload {name}")
+    kind, n, Q = m.group(1), int(m.group(2)), int(m.group(3))
+    lat = lbm.Lattice(n, n, n, Q, dtype)
+    if kind == "tgv":
+        tau = tgv_tau(n, 0.04, 1600.0)
+        lat.set_params(tau)
+        rho, u = tgv_fields(n)
+        desc = {"workload": f"tgv3d_{n}_d3q{Q}_{dtype}", "problem": "periodic 3D Taylor-Green vortex",
+                "u0": 0.04, "Re": 1600, "tau": tau}
+    else:
+        tau = 0.5 + 3.0 * 0.1 * n / 1000.0
+        lat.set_tags(inp.cavity_tags(n))
+        lat.set_params(tau, wall_u=[(0.1, 0.0, 0.0)])
+        rho, u = None, None
+        desc = {"workload": f"cavity_{n}_d3q{Q}_{dtype}", "problem": "lid-driven cavity, Ladd lid",
+                "u_lid": 0.1, "Re": 1000, "tau": tau}
+    lat.init_equilibrium(rho, u)
+    desc.update({"lattice": f"D3Q{Q}", "storage": dtype, "nx": n, "ny": n, "nz": n})
+    return lat, (rho, u), desc
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            self.path = tempfile.mktemp(suffix=".csv")
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                 "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm = float(parts[1].split()[0])
+                smax = float(parts[2].split()[0])
+            except ValueError:
+                continue
+            rows.append((sm, smax, parts[5:9]))
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, flags in rows for k, f in enumerate(flags) if f.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# Timing helpers
+# ---------------------------------------------------------------------------
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("lbm_kernels.cuh", "lbm_internal.cuh"):
+        h.update((ROOT / "paper_2506_09242_gb300" / "csrc" / name).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per collide-stream launch from the committed ncu summary, if
+    it was taken on the current kernel source."""
+    for p in (ROOT / "profiles").glob("*.md"):
+        text = p.read_text()
+        if f"workload: {workload}" not in text:
+            continue
+        m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+        s = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+        if m and s and s.group(1) == kernel_source_hash():
+            return float(m.group(1))
+    return None
+
+
+def measured_peak_hbm():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        try:
+            return float(json.loads(p.read_text())["hbm_gbs"]), "measured"
+        except (KeyError, ValueError):
+            pass
+    return 6800.0, "fallback"
+
+
+def time_lattice(lat, steps: int, warmup: int, inner: int, sync_all=None):
+    """Times ``steps`` benchmark steps (inner lattice steps + reduction).
+
+    Returns (total_ms, mean collide-stream launch ms, reductions)."""
+    import torch
+    for _ in range(warmup):
+        lat.step(inner)
+        lat.reduce()
+    torch.cuda.synchronize()
+    if sync_all:
+        sync_all()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    reds = []
+    t0.record()
+    for k in range(steps):
+        ev[k][0].record()
+        lat.step(inner)
+        ev[k][1].record()
+        reds.append(lat.reduce())
+    t1.record()
+    torch.cuda.synchronize()
+    if sync_all:
+        sync_all()
+    total = t0.elapsed_time(t1)
+    kernel = sum(a.elapsed_time(b) for a, b in ev) / (steps * inner)
+    return total, kernel, reds
+
+
+def time_e2e(lat, fields, steps: int, inner: int):
+    """Each step: upload rho and u from pinned host memory, run ``inner``
+    lattice steps, read the reduction back (all through the C ABI)."""
+    import numpy as np
+    import torch
+    rho, u = fields
+    if rho is None:  # cavity: start from rest with uniform density
+        rho = np.ones((lat.nz, lat.ny, lat.nx))
+        u = np.zeros((3, lat.nz, lat.ny, lat.nx))
+    rho_h = torch.from_numpy(np.ascontiguousarray(rho)).pin_memory()
+    u_h = torch.from_numpy(np.ascontiguousarray(u)).pin_memory()
+    lat.init_equilibrium(rho_h, u_h)  # warm-up of the staging buffers
+    lat.step(inner)
+    lat.reduce()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(steps):
+        lat.init_equilibrium(rho_h, u_h)
+        lat.step(inner)
+        lat.reduce()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t) * 1e3
+    h2d = rho_h.numel() * 8 + u_h.numel() * 8
+    d2h = 12 * 8  # the reduction struct
+    return ms, h2d, d2h
+
+
+def oracle_glups(n: int = 64, target_s: float = 12.0):
+    """FP64 CPU oracle on the host: periodic 3D TGV, D3Q19, n^3, single thread.
+    Returns (GLUPS, seconds, steps, sample description)."""
+    import lbm_inputs as inp
+    import oracle
+    rho, u = inp.tgv3d(n, 0.04)
+    prob = oracle.Problem(19, n, n, n, tau=tgv_tau(n, 0.04, 1600.0))
+    f = prob.init_equilibrium(rho, u)
+    t = time.perf_counter()
+    f = prob.step(f, 1)
+    one = time.perf_counter() - t
+    steps = max(1, int(target_s / max(one, 1e-3)))
+    t = time.perf_counter()
+    prob.step(f, steps)
+    dt = time.perf_counter() - t
+    glups = n ** 3 * steps / dt / 1e9
+    return glups, dt, steps, f"periodic 3D TGV {n}^3 D3Q19 FP64, {steps} steps, single thread"
+
+
+# ---------------------------------------------------------------------------
+# Arms
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import lbm_inputs as inp
+    import oracle
+    n = args.ref_n
+    rho, u = inp.tgv3d(n, 0.04)
+    prob = oracle.Problem(19, n, n, n, tau=tgv_tau(n, 0.04, 1600.0))
+    f = prob.init_equilibrium(rho, u)
+    for _ in range(args.warmup):
+        f = prob.step(f, 1)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        f = prob.step(f, 1)
+    dt = time.perf_counter() - t
+    glups = n ** 3 * args.steps / dt / 1e9
+    sample = f"periodic 3D TGV {n}^3 (bounded sample of the 512^3 workload), D3Q19 FP64 oracle, single thread"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": glups, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "tgv3d_512_d3q19_f32", "sample_n": n, "inner_steps": 1},
+        "cpu_baseline": {"value": glups, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": glups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def error_vs_f64(dtypes=("f32", "f16", "bf16"), n=64, steps=400):
+    """Velocity relative L2 error of each storage type against the FP64 run of
+    the same lattice (periodic 3D TGV n^3, D3Q19, u0 = 0.04, Re = 1600 at n)."""
+    import numpy as np
+    import lbm_inputs as inp
+    from paper_2506_09242_gb300 import lbm
+    rho, u = inp.tgv3d(n, 0.04)
+    tau = tgv_tau(n, 0.04, 1600.0)
+    res = {}
+    ref = None
+    for dt in ("f64",) + tuple(dtypes):
+        with lbm.Lattice(n, n, n, 19, dt) as lat:
+            lat.set_params(tau)
+            lat.init_equilibrium(rho, u)
+            lat.step(steps)
+            _, uu = lat.moments()
+        if dt == "f64":
+            ref = uu
+        else:
+            res[dt] = float(np.linalg.norm(uu - ref) / np.linalg.norm(ref))
+    return {"case": f"periodic 3D TGV {n}^3 D3Q19 Re=1600, {steps} steps, velocity rel. L2 vs the FP64 run",
+            **res}
+
+
+def run_ours(args):
+    import torch
+    from paper_2506_09242_gb300 import _build
+    _build.build()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def sync_all():
+        if dist is not None:
+            dist.barrier()
+
+    lat, fields, desc = make_workload(args.workload, args.dtype)
+    Q = int(desc["lattice"][4:])
+    cells = lat.N
+    sampler = ClockSampler(local)
+    sampler.start()
+    total_ms, kernel_ms, reds = time_lattice(lat, args.steps, args.warmup, args.inner, sync_all)
+    clocks = sampler.stop()
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    updates = cells * args.inner * args.steps * world
+    glups = updates / (total_ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (collide-stream), timed on its stream
+    alg_bytes = 2 * Q * SIZE[args.dtype] * cells
+    achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    traffic = recorded_traffic(desc["workload"])
+
+    e2e_ms, h2d, d2h = time_e2e(lat, fields, max(2, args.steps // 2), args.inner)
+    e2e_steps = max(2, args.steps // 2)
+    e2e_glups = cells * args.inner * e2e_steps * world / (e2e_ms * 1e-3) / 1e9
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+
+    variants = {}
+    errors = None
+    cpu = None
+    if rank == 0 and not args.no_extras:
+        for wl, dt in (("tgv512_d3q19", "f16"), ("tgv512_d3q19", "bf16"), ("cavity256_d3q19", "f32"),
+                       ("tgv512_d3q27", "f32"), ("tgv512_d3q27", "f16")):
+            if (wl, dt) == (args.workload, args.dtype):
+                continue
+            v, _, d = make_workload(wl, dt)
+            tms, kms, _ = time_lattice(v, 5, 3, args.inner)
+            q = int(d["lattice"][4:])
+            ach = 2 * q * SIZE[dt] * v.N / (kms * 1e-3) / 1e9
+            variants[d["workload"]] = {"glups": v.N * args.inner * 5 / (tms * 1e-3) / 1e9,
+                                       "kernel_gbs": ach, "frac_of_peak": ach / peak}
+            v.close()
+            del v
+            torch.cuda.empty_cache()
+        errors = error_vs_f64()
+        if world == 1:
+            g, dt_s, st, sample = oracle_glups()
+            cpu = {"value": g, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    line = {
+        "metric": METRIC, "value": glups, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {**desc, "inner_steps": args.inner, "parallelism": f"replicas{world}",
+                   "l2": f"inputs larger than L2 ({alg_bytes / 1e9:.1f} GB moved per lattice step)",
+                   "step": f"{args.inner} lattice steps + FP64 reduction read back"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "k_collide_stream", "kernel_ms": kernel_ms,
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_glups, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "step": "upload rho,u (FP64, pinned host) + inner lattice steps + reduction read back"},
+        "gpu_launches": args.steps * (args.inner + 2),
+        "clocks": clocks,
+        "mass_drift": abs(reds[-1]["mass"] - reds[0]["mass"]) / reds[0]["mass"] if reds else None,
+        "variants": variants,
+        "errors_vs_f64": errors,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="tgv512_d3q19")
+    ap.add_argument("--dtype", default="f32", choices=sorted(SIZE))
+    ap.add_argument("--inner", type=int, default=20, help="lattice steps per benchmark step")
+    ap.add_argument("--ref-n", type=int, default=64, help="lattice size of the oracle sample")
+    ap.add_argument("--no-extras", action="store_true", help="skip variants, error table and CPU baseline")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,203 @@
+/*
+ * lbm.h -- C ABI of the GB300 lattice Boltzmann hot path.
+ *
+ * The method is the fused collide-and-stream update of a 3D D3Q19 / D3Q27
+ * lattice with structure-of-arrays populations and two-population (A/B)
+ * streaming, cell behaviour chosen by an integer tag per node, and the
+ * density / velocity / kinetic-energy reductions of Latt & Coreixas,
+ * "Multi-GPU Acceleration of PALABOS Fluid Solver using C++ Standard
+ * Parallelism" (Sec. 2.3 for the data layout and the tag mechanism, Sec. 3
+ * for the collision model, boundary conditions and diagnostics).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an lbm_status and never aborts the process; the text
+ *    of the last failure is available from lbm_last_error().  Kernel faults
+ *    surface as LBM_ERR_CUDA at the next call that synchronizes.
+ *  - The caller owns every buffer it passes; the library copies in and out.
+ *    Arguments called "on_device" say whether a pointer is CUDA device memory
+ *    (1) or host memory (0).  Host buffers may be pageable.
+ *  - Cell arrays are unpadded and x-fastest: flat index x + nx*(y + ny*z).
+ *    Vector fields are [3][N] (component-major), populations [Q][N].
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *  - All work of a context is issued on the CUDA stream given at creation.
+ *    Calls marked "asynchronous" return before the GPU has finished.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,      /* invalid argument (size, enum, tag value, tau <= 1/2 ...) */
+    LBM_ERR_OOM = 2,      /* device allocation failed                              */
+    LBM_ERR_CUDA = 3,     /* a CUDA call or kernel failed                          */
+    LBM_ERR_STATE = 4,    /* call not valid in the current state                   */
+    LBM_ERR_UNSTABLE = 5, /* a reduction met a non-finite density or velocity      */
+    LBM_ERR_TIMEOUT = 6   /* lbm_sync gave up waiting                              */
+} lbm_status;
+
+/* Velocity sets.  D3Q19 is the paper's lattice (Sec. 3); D3Q27 is the one it
+ * names as future work (Sec. 5).  Velocity order: 0 rest; 1..6 = +x -x +y -y
+ * +z -z; 7..18 = (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1)
+ * (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1); D3Q27 adds 19..26 =
+ * (1,1,1) (-1,-1,-1) (1,1,-1) (-1,-1,1) (1,-1,1) (-1,1,-1) (-1,1,1)
+ * (1,-1,-1).  Direction i+1 is the opposite of direction i for odd i. */
+typedef enum { LBM_D3Q19 = 19, LBM_D3Q27 = 27 } lbm_lattice;
+
+/* Storage type of the populations.  Every type stores the offset-stripped
+ * deviation h_i = f_i - w_i (Skordos' shift, Sec. 3); arithmetic runs in FP64
+ * for LBM_F64 and in FP32 for the others; reductions accumulate in FP64.
+ * The 16-bit types round to nearest-even on store. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16_SHIFTED = 2, LBM_BF16_SHIFTED = 3 } lbm_dtype;
+
+/* Node tags (Sec. 2.3.2: one integer per node selects the node's model). */
+enum {
+    LBM_TAG_FLUID = 0,  /* fluid node, collision only                               */
+    LBM_TAG_FORCED = 1, /* fluid node with the body force of lbm_params.force       */
+    LBM_TAG_SOLID = 2,  /* resting wall: halfway bounce-back, never updated         */
+    LBM_TAG_WALL0 = 3,  /* LBM_TAG_WALL0 + k: moving wall k (Ladd), never updated   */
+    LBM_NWALLS = 8,
+    LBM_NTAGS = LBM_TAG_WALL0 + LBM_NWALLS
+};
+
+/* Collision closures. */
+typedef enum {
+    LBM_CLOSURE_BGK = 0,         /* BGK with the 2nd-order weighted equilibrium (Sec. 3.1) */
+    LBM_CLOSURE_SMAGORINSKY = 1, /* BGK with a Smagorinsky eddy viscosity (Sec. 2.3.2)     */
+    LBM_CLOSURE_MLP = 2,         /* BGK with a learned per-cell relaxation-time correction */
+    LBM_CLOSURE_STREAM_ONLY = 3  /* no collision: pure streaming, for verification        */
+} lbm_closure;
+
+/* Optional device allocator.  alloc returns device memory of at least
+ * "bytes" bytes usable on "stream" (NULL on failure); free releases it.  A
+ * NULL allocator in lbm_create selects cudaMalloc / cudaFree. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} lbm_allocator;
+
+/* Model parameters (lattice units).
+ *  tau      BGK relaxation time, tau > 1/2; viscosity nu = (tau - 1/2)/3.
+ *  force    body force g applied to LBM_TAG_FORCED nodes with Guo's scheme.
+ *  closure  an lbm_closure value.
+ *  cs_smag  Smagorinsky constant (closure 1).
+ *  wall_u   velocity of moving wall k, used by Ladd's bounce-back
+ *           f_i(x) = f*_opp(i)(x) + 6 w_i rho_wall (c_i . wall_u[k]).
+ *  rho_wall density in Ladd's wall term (the reference density, 1). */
+typedef struct {
+    double tau;
+    double force[3];
+    int closure;
+    double cs_smag;
+    double wall_u[LBM_NWALLS][3];
+    double rho_wall;
+} lbm_params;
+
+/* Sums over fluid nodes (tags FLUID and FORCED), accumulated in FP64 from
+ * the stored post-collision populations: rho = sum f_i and
+ * u = (sum c_i f_i - rho g / 2) / rho on FORCED nodes (without the g term
+ * elsewhere), i.e. the density and velocity that the last collision used. */
+typedef struct {
+    double mass;         /* sum rho                                   */
+    double mom[3];       /* sum rho u                                 */
+    double vel[3];       /* sum u                                     */
+    double ke;           /* sum |u|^2 / 2   (k of Sec. 3.1 times N)   */
+    double ke_rho;       /* sum rho |u|^2 / 2                         */
+    double umax;         /* max |u|                                   */
+    long long n_fluid;   /* number of fluid nodes                     */
+    long long nonfinite; /* fluid nodes with non-finite rho or u      */
+} lbm_reduction;
+
+/* Creates a lattice of nx*ny*nz nodes (each >= 1, nx*ny*nz < 2^31 after
+ * padding x to a multiple of 32), allocates both population arrays on the
+ * device, sets every tag to FLUID, the parameters to tau = 1, no force, BGK,
+ * rho_wall = 1, and the state to rest (f = w).  stream: a cudaStream_t, or
+ * NULL for the legacy default stream.  On failure *out is NULL and nothing
+ * stays allocated.  Errors: ARG, OOM, CUDA. */
+lbm_status lbm_create(int nx, int ny, int nz, lbm_lattice lattice, lbm_dtype dtype, const lbm_allocator *alloc,
+                      void *stream, lbm_ctx **out);
+
+/* Waits for the context's stream and frees everything it owns.  NULL is a
+ * no-op. */
+lbm_status lbm_destroy(lbm_ctx *ctx);
+
+/* Sets the model parameters.  Errors: ARG (tau <= 1/2 or not finite,
+ * unknown closure, cs_smag < 0). */
+lbm_status lbm_set_params(lbm_ctx *ctx, const lbm_params *p);
+
+/* Sets the tag of every node (N bytes, values below LBM_NTAGS), derives the
+ * per-node "next to a wall" flag and the tag census used to pick the kernel
+ * variant (the analogue of the paper's hand-picked collision kernel,
+ * Sec. 2.3.2).  Synchronizes.  Errors: ARG (a tag value >= LBM_NTAGS; the
+ * previous tags stay in force), CUDA. */
+lbm_status lbm_set_tags(lbm_ctx *ctx, const uint8_t *tags, int on_device);
+
+/* Copies the tags out (N bytes).  Synchronizes. */
+lbm_status lbm_get_tags(lbm_ctx *ctx, uint8_t *tags, int on_device);
+
+/* Number of nodes per tag value, counts[LBM_NTAGS]. */
+lbm_status lbm_tag_census(lbm_ctx *ctx, long long *counts);
+
+/* Equilibrium initial state (Sec. 3.1, used for the Taylor-Green vortex):
+ * f*_i = f_eq_i(rho, u) on every node, written to both population arrays.
+ * rho: N values or NULL (uniform 1); u: [3][N] or NULL (rest).  Resets the
+ * step counter.  Asynchronous for device inputs.  Errors: CUDA, OOM. */
+lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u, int on_device);
+
+/* Advances n >= 0 steps of fused pull collide-and-stream (Sec. 2.3.1):
+ * f_i(x) = f*_i(x - c_i), with bounce-back from SOLID sources and Ladd's
+ * term from WALL sources, then collision on every fluid node, written to the
+ * other array.  Asynchronous.  Errors: ARG (n < 0), STATE (MLP closure
+ * without weights), CUDA (launch failure). */
+lbm_status lbm_step(lbm_ctx *ctx, int n);
+
+/* Number of steps taken since the last initialisation. */
+lbm_status lbm_step_count(lbm_ctx *ctx, long long *steps);
+
+/* Density rho[N] and velocity u[3][N] of every node, from the stored
+ * post-collision populations (see lbm_reduction).  Solid and wall nodes
+ * report 0.  Either pointer may be NULL.  Synchronizes. */
+lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *u, int on_device);
+
+/* FP64 domain sums over the fluid nodes (the transform-reduce of Sec. 2.2),
+ * deterministic for a given lattice size.  Synchronizes.  Returns
+ * LBM_ERR_UNSTABLE, with *out filled, when any fluid node has a non-finite
+ * density or velocity. */
+lbm_status lbm_reduce(lbm_ctx *ctx, lbm_reduction *out);
+
+/* Waits up to timeout_ms (< 0: no limit) for the context's stream; returns
+ * LBM_ERR_TIMEOUT if the work is still running then (the work continues),
+ * LBM_ERR_CUDA if it failed. */
+lbm_status lbm_sync(lbm_ctx *ctx, int timeout_ms);
+
+/* Unshifted FP64 populations f[Q][N] of the current state (the
+ * post-collision set of the last step).  Synchronizes. */
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int on_device);
+
+/* Replaces the state by f[Q][N] (unshifted FP64), rounded to the storage
+ * type (nearest-even, through FP32 for the 16-bit types), in both arrays.
+ * Does not reset the step counter.  Asynchronous for device inputs. */
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device);
+
+/* Library-side sizes: bytes of one population array, x pitch in nodes,
+ * number of populations.  Any pointer may be NULL. */
+lbm_status lbm_info(lbm_ctx *ctx, size_t *population_bytes, int *pitch_x, int *q);
+
+/* Text of the last failure of ctx (or of a call without a context, for
+ * ctx == NULL).  Never NULL; valid until the next call on the same ctx. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

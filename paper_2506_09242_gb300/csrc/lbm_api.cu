@@ -1,0 +1,557 @@
+// lbm_api.cu -- the C ABI of lbm.h: context, validation, memory, dispatch to
+// the per-storage-type launchers, and the storage-independent kernels (tag
+// preparation, reduction second pass).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <new>
+#include <string>
+#include <thread>
+
+#include "lbm_kernels.cuh"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    int nx = 0, ny = 0, nz = 0, px = 0, Q = 0;
+    lbm_dtype dtype = LBM_F32;
+    Grid g{};
+    size_t elem = 4;            // bytes per stored population value
+    size_t pop_bytes = 0;       // bytes of one population array (Q planes)
+    void *A = nullptr, *B = nullptr;
+    uint8_t *tags = nullptr;    // internal padded tags
+    double *partials = nullptr; // kRedBlocks x kRedSlots reduction scratch
+    double *red_out = nullptr;  // kRedSlots final sums
+    unsigned long long *census_dev = nullptr;  // LBM_NTAGS + 1 counters
+    cudaStream_t stream = nullptr;
+    lbm_allocator alloc{};
+    bool has_alloc = false;
+    lbm_params params{};
+    long long census[LBM_NTAGS] = {};
+    bool general = false;
+    long long steps = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err;  // errors of calls without a context
+
+lbm_status fail(lbm_ctx *ctx, lbm_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    (ctx ? ctx->err : g_err) = buf;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_ctx *ctx, cudaError_t e, const char *what)
+{
+    return fail(ctx, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(ctx, expr, what)                          \
+    do {                                                   \
+        cudaError_t e_ = (expr);                           \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+void *dev_alloc(lbm_ctx *ctx, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (ctx->has_alloc) return ctx->alloc.alloc(bytes, (void *)ctx->stream, ctx->alloc.user);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(lbm_ctx *ctx, void *p, size_t bytes)
+{
+    if (!p) return;
+    if (bytes == 0) bytes = 16;
+    if (ctx->has_alloc)
+        ctx->alloc.free(p, bytes, (void *)ctx->stream, ctx->alloc.user);
+    else
+        cudaFree(p);
+}
+
+// RAII temporary device buffer.
+struct Tmp {
+    lbm_ctx *ctx;
+    void *p = nullptr;
+    size_t bytes = 0;
+    Tmp(lbm_ctx *c, size_t b) : ctx(c), bytes(b) { p = b ? dev_alloc(c, b) : nullptr; }
+    ~Tmp() { dev_free(ctx, p, bytes); }
+};
+
+Launch make_launch(lbm_ctx *ctx)
+{
+    Launch L;
+    L.Q = ctx->Q;
+    L.g = ctx->g;
+    L.A = ctx->A;
+    L.B = ctx->B;
+    L.tags = ctx->tags;
+    L.general = ctx->general;
+    L.closure = ctx->params.closure;
+    L.mlp = nullptr;
+    L.stream = ctx->stream;
+    return L;
+}
+
+template <typename F> cudaError_t by_dtype(lbm_dtype d, F &&f)
+{
+    switch (d) {
+    case LBM_F64: return f((double *)nullptr);
+    case LBM_F32: return f((float *)nullptr);
+    case LBM_F16_SHIFTED: return f((__half *)nullptr);
+    case LBM_BF16_SHIFTED: return f((__nv_bfloat16 *)nullptr);
+    }
+    return cudaErrorInvalidValue;
+}
+
+lbm_status wait_stream(lbm_ctx *ctx, int timeout_ms)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(ctx->stream);
+        if (e == cudaSuccess) return LBM_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(ctx, e, "stream");
+        if (timeout_ms >= 0) {
+            const auto ms =
+                std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+            if (ms >= timeout_ms) return fail(ctx, LBM_ERR_TIMEOUT, "stream still busy after %d ms", timeout_ms);
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+// Synchronizing calls wait without limit: a kernel of this library always
+// terminates, so only a fault can end the wait early.
+lbm_status sync(lbm_ctx *ctx) { return wait_stream(ctx, -1); }
+
+bool valid_params(const lbm_params *p, std::string &why)
+{
+    if (!(p->tau > 0.5) || !isfinite(p->tau)) return why = "tau must be finite and > 1/2", false;
+    if (p->closure < LBM_CLOSURE_BGK || p->closure > LBM_CLOSURE_STREAM_ONLY) return why = "unknown closure", false;
+    if (!(p->cs_smag >= 0.0) || !isfinite(p->cs_smag)) return why = "cs_smag must be >= 0", false;
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(p->force[a])) return why = "force must be finite", false;
+    for (int k = 0; k < LBM_NWALLS; ++k)
+        for (int a = 0; a < 3; ++a)
+            if (!isfinite(p->wall_u[k][a])) return why = "wall velocity must be finite", false;
+    if (!isfinite(p->rho_wall)) return why = "rho_wall must be finite", false;
+    return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Storage-independent kernels.
+// ---------------------------------------------------------------------------
+namespace lbm {
+
+__global__ void __launch_bounds__(kRedThreads) k_reduce_final(const double *__restrict__ partials, int nblocks,
+                                                             double *__restrict__ out)
+{
+    double acc[kRedSlots];
+#pragma unroll
+    for (int k = 0; k < kRedSlots; ++k) acc[k] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < kRedSlots; ++k)
+            acc[k] = (k == 9) ? fmax(acc[k], partials[(long long)b * kRedSlots + k])
+                              : acc[k] + partials[(long long)b * kRedSlots + k];
+    block_reduce_slots(acc);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < kRedSlots; ++k) out[k] = acc[k];
+}
+
+// Copies user tags into the padded internal array, flags fluid nodes that
+// pull from a SOLID or WALL neighbour, and counts tag values (slot LBM_NTAGS
+// counts invalid values).
+template <int Q>
+__global__ void k_prepare_tags(Grid g, const uint8_t *__restrict__ user, uint8_t *__restrict__ tags,
+                               unsigned long long *__restrict__ census)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    Nbr nb;
+    nb.init(g, x, y, z);
+    const long long n = x + (long long)g.nx * (y + (long long)g.ny * z);
+    const unsigned t = user[n];
+    if (t >= LBM_NTAGS) {
+        atomicAdd(&census[LBM_NTAGS], 1ull);
+        return;
+    }
+    atomicAdd(&census[t], 1ull);
+    bool near = false;
+    if (!is_wall_tag(t)) {
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            // source node x - c_i, read from the unpadded user array
+            const int xs = nb.xs[1 - cvel(i, 0)];
+            const int r = nb.row[1 - cvel(i, 1)][1 - cvel(i, 2)] / g.px;  // z*ny + y of the source
+            near |= is_wall_tag(user[xs + (long long)g.nx * r]);
+        }
+    }
+    tags[nb.self] = (uint8_t)(t | (near ? kNearWall : 0));
+}
+
+// User view of the internal tags: unpadded, flag bit cleared.
+__global__ void k_gather_tags(Grid g, const uint8_t *__restrict__ tags, uint8_t *__restrict__ out)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    out[x + (long long)g.nx * (y + (long long)g.ny * z)] = tags[(z * g.ny + y) * g.px + x] & kTagMask;
+}
+
+cudaError_t launch_gather_tags(const Grid &g, const uint8_t *tags, uint8_t *out, cudaStream_t s)
+{
+    dim3 grid, block;
+    node_launch_shape(g, grid, block);
+    k_gather_tags<<<grid, block, 0, s>>>(g, tags, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prepare_tags(int Q, const Grid &g, const uint8_t *user, uint8_t *tags, unsigned long long *census,
+                                cudaStream_t s)
+{
+    dim3 grid, block;
+    node_launch_shape(g, grid, block);
+    if (Q == 19)
+        k_prepare_tags<19><<<grid, block, 0, s>>>(g, user, tags, census);
+    else
+        k_prepare_tags<27><<<grid, block, 0, s>>>(g, user, tags, census);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm
+
+// ---------------------------------------------------------------------------
+// C ABI.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+lbm_status lbm_destroy(lbm_ctx *ctx)
+{
+    if (!ctx) return LBM_OK;
+    cudaStreamSynchronize(ctx->stream);
+    cudaGetLastError();
+    dev_free(ctx, ctx->A, ctx->pop_bytes);
+    dev_free(ctx, ctx->B, ctx->pop_bytes);
+    dev_free(ctx, ctx->tags, (size_t)ctx->g.sN);
+    dev_free(ctx, ctx->partials, sizeof(double) * kRedBlocks * kRedSlots);
+    dev_free(ctx, ctx->red_out, sizeof(double) * kRedSlots);
+    dev_free(ctx, ctx->census_dev, sizeof(unsigned long long) * (LBM_NTAGS + 1));
+    delete ctx;
+    return LBM_OK;
+}
+
+lbm_status lbm_create(int nx, int ny, int nz, lbm_lattice lattice, lbm_dtype dtype, const lbm_allocator *alloc,
+                      void *stream, lbm_ctx **out)
+{
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_ERR_ARG, "lattice sizes must be >= 1");
+    if (lattice != LBM_D3Q19 && lattice != LBM_D3Q27) return fail(nullptr, LBM_ERR_ARG, "unknown lattice %d", (int)lattice);
+    if (dtype < LBM_F64 || dtype > LBM_BF16_SHIFTED) return fail(nullptr, LBM_ERR_ARG, "unknown dtype %d", (int)dtype);
+    if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, LBM_ERR_ARG, "allocator needs alloc and free");
+    if (nz > 65535) return fail(nullptr, LBM_ERR_ARG, "nz must be <= 65535");
+    const long long px = ((long long)nx + 31) / 32 * 32;
+    const long long cells = px * ny * nz;
+    if (cells >= (1ll << 31) - 256) return fail(nullptr, LBM_ERR_ARG, "lattice too large (padded nodes >= 2^31)");
+
+    lbm_ctx *ctx = new (std::nothrow) lbm_ctx();
+    if (!ctx) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+    ctx->nx = nx;
+    ctx->ny = ny;
+    ctx->nz = nz;
+    ctx->px = (int)px;
+    ctx->Q = (int)lattice;
+    ctx->dtype = dtype;
+    ctx->elem = dtype == LBM_F64 ? 8 : dtype == LBM_F32 ? 4 : 2;
+    ctx->g.nx = nx;
+    ctx->g.ny = ny;
+    ctx->g.nz = nz;
+    ctx->g.px = (int)px;
+    ctx->g.sN = (cells + 255) / 256 * 256;  // planes start 512-byte aligned or better
+    ctx->g.N = (long long)nx * ny * nz;
+    ctx->pop_bytes = (size_t)ctx->Q * (size_t)ctx->g.sN * ctx->elem;
+    ctx->stream = (cudaStream_t)stream;
+    if (alloc) {
+        ctx->alloc = *alloc;
+        ctx->has_alloc = true;
+    }
+    ctx->params.tau = 1.0;
+    ctx->params.closure = LBM_CLOSURE_BGK;
+    ctx->params.rho_wall = 1.0;
+
+    ctx->A = dev_alloc(ctx, ctx->pop_bytes);
+    ctx->B = dev_alloc(ctx, ctx->pop_bytes);
+    ctx->tags = (uint8_t *)dev_alloc(ctx, (size_t)ctx->g.sN);
+    ctx->partials = (double *)dev_alloc(ctx, sizeof(double) * kRedBlocks * kRedSlots);
+    ctx->red_out = (double *)dev_alloc(ctx, sizeof(double) * kRedSlots);
+    ctx->census_dev = (unsigned long long *)dev_alloc(ctx, sizeof(unsigned long long) * (LBM_NTAGS + 1));
+    if (!ctx->A || !ctx->B || !ctx->tags || !ctx->partials || !ctx->red_out || !ctx->census_dev) {
+        lbm_destroy(ctx);
+        return fail(nullptr, LBM_ERR_OOM, "device allocation of %.3f GB failed",
+                    (2.0 * ctx->pop_bytes + ctx->g.sN) / 1e9);
+    }
+    cudaError_t e = cudaMemsetAsync(ctx->tags, 0, (size_t)ctx->g.sN, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->A, 0, ctx->pop_bytes, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->B, 0, ctx->pop_bytes, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        lbm_destroy(ctx);
+        return cuda_fail(nullptr, e, "lbm_create");
+    }
+    ctx->census[LBM_TAG_FLUID] = ctx->g.N;
+    *out = ctx;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_params(lbm_ctx *ctx, const lbm_params *p)
+{
+    if (!ctx || !p) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    std::string why;
+    if (!valid_params(p, why)) return fail(ctx, LBM_ERR_ARG, "%s", why.c_str());
+    if (p->closure == LBM_CLOSURE_MLP) return fail(ctx, LBM_ERR_ARG, "MLP closure is not available in this build");
+    ctx->params = *p;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_tags(lbm_ctx *ctx, const uint8_t *tags, int on_device)
+{
+    if (!ctx || !tags) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    const size_t n = (size_t)ctx->g.N;
+    Tmp user(ctx, n);
+    Tmp scratch(ctx, (size_t)ctx->g.sN);
+    if (!user.p || !scratch.p) return fail(ctx, LBM_ERR_OOM, "tag staging allocation failed");
+    CUDA_TRY(ctx, cudaMemcpyAsync(user.p, tags, n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream),
+             "tag copy");
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->census_dev, 0, sizeof(unsigned long long) * (LBM_NTAGS + 1), ctx->stream),
+             "census reset");
+    CUDA_TRY(ctx, cudaMemsetAsync(scratch.p, 0, (size_t)ctx->g.sN, ctx->stream), "tag reset");
+    CUDA_TRY(ctx, launch_prepare_tags(ctx->Q, ctx->g, (const uint8_t *)user.p, (uint8_t *)scratch.p, ctx->census_dev, ctx->stream),
+             "tag preparation");
+    unsigned long long c[LBM_NTAGS + 1];
+    CUDA_TRY(ctx, cudaMemcpyAsync(c, ctx->census_dev, sizeof c, cudaMemcpyDeviceToHost, ctx->stream), "census copy");
+    lbm_status s = sync(ctx);
+    if (s != LBM_OK) return s;
+    if (c[LBM_NTAGS] != 0) return fail(ctx, LBM_ERR_ARG, "%llu tag values >= %d", c[LBM_NTAGS], (int)LBM_NTAGS);
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->tags, scratch.p, (size_t)ctx->g.sN, cudaMemcpyDeviceToDevice, ctx->stream),
+             "tag install");
+    bool general = false;
+    for (int k = 0; k < LBM_NTAGS; ++k) {
+        ctx->census[k] = (long long)c[k];
+        if (k != LBM_TAG_FLUID && c[k]) general = true;
+    }
+    ctx->general = general;
+    return sync(ctx);
+}
+
+lbm_status lbm_get_tags(lbm_ctx *ctx, uint8_t *tags, int on_device)
+{
+    if (!ctx || !tags) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    Tmp t(ctx, on_device ? 0 : (size_t)ctx->g.N);
+    if (!on_device && !t.p) return fail(ctx, LBM_ERR_OOM, "staging allocation failed");
+    uint8_t *dst = on_device ? tags : (uint8_t *)t.p;
+    CUDA_TRY(ctx, launch_gather_tags(ctx->g, ctx->tags, dst, ctx->stream), "tag gather");
+    if (!on_device)
+        CUDA_TRY(ctx, cudaMemcpyAsync(tags, t.p, (size_t)ctx->g.N, cudaMemcpyDeviceToHost, ctx->stream), "tag copy");
+    return sync(ctx);
+}
+
+lbm_status lbm_tag_census(lbm_ctx *ctx, long long *counts)
+{
+    if (!ctx || !counts) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    for (int k = 0; k < LBM_NTAGS; ++k) counts[k] = ctx->census[k];
+    return LBM_OK;
+}
+
+lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u, int on_device)
+{
+    if (!ctx) return fail(ctx, LBM_ERR_ARG, "NULL context");
+    const size_t nb = sizeof(double) * (size_t)ctx->g.N;
+    Launch L = make_launch(ctx);
+    lbm_status s = LBM_OK;
+    if (on_device || (!rho && !u)) {
+        CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
+                     using S = std::remove_pointer_t<decltype(tag)>;
+                     return launch_init<S>(L, rho, u);
+                 }),
+                 "init");
+    } else {
+        Tmp r(ctx, rho ? nb : 0), v(ctx, u ? 3 * nb : 0);
+        if ((rho && !r.p) || (u && !v.p)) return fail(ctx, LBM_ERR_OOM, "staging allocation failed");
+        if (rho) CUDA_TRY(ctx, cudaMemcpyAsync(r.p, rho, nb, cudaMemcpyHostToDevice, ctx->stream), "rho copy");
+        if (u) CUDA_TRY(ctx, cudaMemcpyAsync(v.p, u, 3 * nb, cudaMemcpyHostToDevice, ctx->stream), "u copy");
+        CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
+                     using S = std::remove_pointer_t<decltype(tag)>;
+                     return launch_init<S>(L, rho ? (const double *)r.p : nullptr, u ? (const double *)v.p : nullptr);
+                 }),
+                 "init");
+        s = sync(ctx);
+    }
+    ctx->steps = 0;
+    return s;
+}
+
+lbm_status lbm_step(lbm_ctx *ctx, int n)
+{
+    if (!ctx) return fail(ctx, LBM_ERR_ARG, "NULL context");
+    if (n < 0) return fail(ctx, LBM_ERR_ARG, "n must be >= 0");
+    for (int k = 0; k < n; ++k) {
+        Launch L = make_launch(ctx);
+        CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
+                     using S = std::remove_pointer_t<decltype(tag)>;
+                     return launch_step<S>(L, ctx->params);
+                 }),
+                 "collide-stream launch");
+        std::swap(ctx->A, ctx->B);
+        ++ctx->steps;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_step_count(lbm_ctx *ctx, long long *steps)
+{
+    if (!ctx || !steps) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    *steps = ctx->steps;
+    return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *u, int on_device)
+{
+    if (!ctx) return fail(ctx, LBM_ERR_ARG, "NULL context");
+    if (!rho && !u) return LBM_OK;
+    const size_t nb = sizeof(double) * (size_t)ctx->g.N;
+    Launch L = make_launch(ctx);
+    if (on_device) {
+        CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
+                     using S = std::remove_pointer_t<decltype(tag)>;
+                     return launch_moments<S>(L, ctx->params, rho, u);
+                 }),
+                 "moments");
+        return sync(ctx);
+    }
+    Tmp r(ctx, rho ? nb : 0), v(ctx, u ? 3 * nb : 0);
+    if ((rho && !r.p) || (u && !v.p)) return fail(ctx, LBM_ERR_OOM, "staging allocation failed");
+    CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
+                 using S = std::remove_pointer_t<decltype(tag)>;
+                 return launch_moments<S>(L, ctx->params, rho ? (double *)r.p : nullptr, u ? (double *)v.p : nullptr);
+             }),
+             "moments");
+    if (rho) CUDA_TRY(ctx, cudaMemcpyAsync(rho, r.p, nb, cudaMemcpyDeviceToHost, ctx->stream), "rho copy");
+    if (u) CUDA_TRY(ctx, cudaMemcpyAsync(u, v.p, 3 * nb, cudaMemcpyDeviceToHost, ctx->stream), "u copy");
+    return sync(ctx);
+}
+
+lbm_status lbm_reduce(lbm_ctx *ctx, lbm_reduction *out)
+{
+    if (!ctx || !out) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    const long long total = (long long)ctx->g.nz * ctx->g.ny * ctx->g.px;
+    long long nb = (total + kRedThreads - 1) / kRedThreads;
+    if (nb > kRedBlocks) nb = kRedBlocks;
+    Launch L = make_launch(ctx);
+    CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
+                 using S = std::remove_pointer_t<decltype(tag)>;
+                 return launch_reduce<S>(L, ctx->params, ctx->partials, (int)nb, ctx->red_out);
+             }),
+             "reduce");
+    double r[kRedSlots];
+    CUDA_TRY(ctx, cudaMemcpyAsync(r, ctx->red_out, sizeof r, cudaMemcpyDeviceToHost, ctx->stream), "reduce copy");
+    lbm_status s = sync(ctx);
+    if (s != LBM_OK) return s;
+    out->n_fluid = (long long)r[10];
+    out->nonfinite = (long long)r[11];
+    out->mass = (double)(out->n_fluid - out->nonfinite) + r[0];
+    for (int a = 0; a < 3; ++a) {
+        out->mom[a] = r[1 + a];
+        out->vel[a] = r[4 + a];
+    }
+    out->ke = r[7];
+    out->ke_rho = r[8];
+    out->umax = r[9];
+    if (out->nonfinite) return fail(ctx, LBM_ERR_UNSTABLE, "%lld fluid nodes have non-finite moments", out->nonfinite);
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx *ctx, int timeout_ms)
+{
+    if (!ctx) return fail(ctx, LBM_ERR_ARG, "NULL context");
+    return wait_stream(ctx, timeout_ms);
+}
+
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int on_device)
+{
+    if (!ctx || !f) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    const size_t nb = sizeof(double) * (size_t)ctx->g.N;
+    Tmp plane(ctx, on_device ? 0 : nb);
+    if (!on_device && !plane.p) return fail(ctx, LBM_ERR_OOM, "staging allocation failed");
+    Launch L = make_launch(ctx);
+    for (int i = 0; i < ctx->Q; ++i) {
+        double *dst = on_device ? f + (size_t)i * ctx->g.N : (double *)plane.p;
+        CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
+                     using S = std::remove_pointer_t<decltype(tag)>;
+                     return launch_get_pop<S>(L, i, dst);
+                 }),
+                 "population gather");
+        if (!on_device) {
+            CUDA_TRY(ctx, cudaMemcpyAsync(f + (size_t)i * ctx->g.N, plane.p, nb, cudaMemcpyDeviceToHost, ctx->stream),
+                     "population copy");
+        }
+    }
+    return sync(ctx);
+}
+
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device)
+{
+    if (!ctx || !f) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    const size_t nb = sizeof(double) * (size_t)ctx->g.N;
+    Tmp plane(ctx, on_device ? 0 : nb);
+    if (!on_device && !plane.p) return fail(ctx, LBM_ERR_OOM, "staging allocation failed");
+    Launch L = make_launch(ctx);
+    for (int i = 0; i < ctx->Q; ++i) {
+        const double *src = f + (size_t)i * ctx->g.N;
+        if (!on_device) {
+            CUDA_TRY(ctx, cudaMemcpyAsync(plane.p, src, nb, cudaMemcpyHostToDevice, ctx->stream), "population copy");
+            src = (const double *)plane.p;
+        }
+        CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
+                     using S = std::remove_pointer_t<decltype(tag)>;
+                     return launch_set_pop<S>(L, i, src);
+                 }),
+                 "population scatter");
+    }
+    return on_device ? LBM_OK : sync(ctx);
+}
+
+lbm_status lbm_info(lbm_ctx *ctx, size_t *population_bytes, int *pitch_x, int *q)
+{
+    if (!ctx) return fail(ctx, LBM_ERR_ARG, "NULL context");
+    if (population_bytes) *population_bytes = ctx->pop_bytes;
+    if (pitch_x) *pitch_x = ctx->px;
+    if (q) *q = ctx->Q;
+    return LBM_OK;
+}
+
+}  // extern "C"

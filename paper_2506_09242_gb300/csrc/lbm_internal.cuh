@@ -1,0 +1,141 @@
+// lbm_internal.cuh -- shared definitions of the CUDA library (not part of the
+// C ABI): lattice tables, storage traits, kernel argument structs and the
+// launcher declarations implemented once per storage type.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm.h"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Lattice tables.  Order as documented in lbm.h; weights from |c|^2:
+// D3Q19 1/3, 1/18, 1/36; D3Q27 8/27, 2/27, 1/54, 1/216.  Called with
+// compile-time indices inside unrolled loops, so every entry folds to an
+// immediate.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int cvel(int i, int a)
+{
+    constexpr int t[27 * 3] = {0,  0,  0,                                          //
+                               1,  0,  0,  -1, 0,  0,  0,  1,  0,  0,  -1, 0,  0,  0,  1,  0,  0,  -1,  //
+                               1,  1,  0,  -1, -1, 0,  1,  -1, 0,  -1, 1,  0,                         //
+                               1,  0,  1,  -1, 0,  -1, 1,  0,  -1, -1, 0,  1,                         //
+                               0,  1,  1,  0,  -1, -1, 0,  1,  -1, 0,  -1, 1,                         //
+                               1,  1,  1,  -1, -1, -1, 1,  1,  -1, -1, -1, 1,                         //
+                               1,  -1, 1,  -1, 1,  -1, -1, 1,  1,  1,  -1, -1};
+    return t[3 * i + a];
+}
+
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+__host__ __device__ constexpr int cnorm2(int i)
+{
+    return cvel(i, 0) * cvel(i, 0) + cvel(i, 1) * cvel(i, 1) + cvel(i, 2) * cvel(i, 2);
+}
+
+template <typename T>
+__host__ __device__ constexpr T wgt(int Q, int i)
+{
+    return Q == 19 ? (cnorm2(i) == 0 ? T(1) / T(3) : cnorm2(i) == 1 ? T(1) / T(18) : T(1) / T(36))
+                   : (cnorm2(i) == 0   ? T(8) / T(27)
+                      : cnorm2(i) == 1 ? T(2) / T(27)
+                      : cnorm2(i) == 2 ? T(1) / T(54)
+                                       : T(1) / T(216));
+}
+
+// ---------------------------------------------------------------------------
+// Storage traits: load h = f - w into the compute type, store rounded.
+// ---------------------------------------------------------------------------
+template <typename S> struct Store;
+template <> struct Store<double> {
+    using T = double;
+    static __device__ __forceinline__ T ld(const double *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(double *p, T v) { *p = v; }
+    static __device__ __forceinline__ double from_f64(double v) { return v; }
+};
+template <> struct Store<float> {
+    using T = float;
+    static __device__ __forceinline__ T ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float *p, T v) { *p = v; }
+    static __device__ __forceinline__ float from_f64(double v) { return (float)v; }
+};
+template <> struct Store<__half> {
+    using T = float;
+    static __device__ __forceinline__ T ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__half *p, T v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ __half from_f64(double v) { return __float2half_rn((float)v); }
+};
+template <> struct Store<__nv_bfloat16> {
+    using T = float;
+    static __device__ __forceinline__ T ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, T v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ __nv_bfloat16 from_f64(double v) { return __float2bfloat16_rn((float)v); }
+};
+
+// Internal tag byte: the user tag in the low 7 bits, bit 7 set on fluid
+// nodes that have a SOLID or WALL node among their Q neighbours.
+constexpr uint8_t kNearWall = 0x80;
+constexpr uint8_t kTagMask = 0x7f;
+
+__host__ __device__ constexpr bool is_wall_tag(unsigned t) { return t >= LBM_TAG_SOLID && t < LBM_NTAGS; }
+
+// Lattice geometry as the kernels see it: x padded to px, planes of sN.
+struct Grid {
+    int nx, ny, nz, px;
+    long long sN;   // elements per population plane (>= nz*ny*px)
+    long long N;    // nx*ny*nz (unpadded count)
+};
+
+// Parameters in the compute type.
+template <typename T> struct KParams {
+    T omega;                      // 1 / tau
+    T tau;                        // tau
+    T force[3];                   // g
+    T smag18;                     // 18 Cs^2
+    T wall6[LBM_NWALLS][3];       // 6 rho_wall u_wall (Ladd term = w_i c_i . wall6)
+};
+
+// Number of FP64 slots of one reduction partial.
+constexpr int kRedSlots = 12;  // dmass, mom[3], vel[3], ke, ke_rho, umax, n_fluid, nonfinite
+constexpr int kRedBlocks = 1216;  // 152 SMs x 8
+constexpr int kRedThreads = 256;
+
+// MLP closure parameters as the collide kernel reads them (device memory).
+constexpr int kMlpIn = 7;
+constexpr int kMlpH = 32;
+constexpr int kMlpNParam = kMlpH * kMlpIn + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;  // 1345
+
+// Launch arguments common to the per-dtype launchers.
+struct Launch {
+    int Q;
+    Grid g;
+    const void *A;
+    void *B;
+    const uint8_t *tags;      // internal padded tags
+    bool general;             // tags present (not all FLUID)
+    int closure;
+    const void *mlp;          // device MLP block (closure 2)
+    cudaStream_t stream;
+};
+
+// Per-storage-type launchers (one translation unit per type).
+template <typename S> cudaError_t launch_step(const Launch &L, const lbm_params &p);
+template <typename S>
+cudaError_t launch_reduce(const Launch &L, const lbm_params &p, double *partials, int nblocks, double *out);
+template <typename S>
+cudaError_t launch_moments(const Launch &L, const lbm_params &p, double *rho, double *u);
+template <typename S>
+cudaError_t launch_init(const Launch &L, const double *rho, const double *u);
+template <typename S> cudaError_t launch_get_pop(const Launch &L, int i, double *f_plane);
+template <typename S> cudaError_t launch_set_pop(const Launch &L, int i, const double *f_plane);
+
+// Storage-type independent kernels (lbm_api.cu).
+cudaError_t launch_prepare_tags(int Q, const Grid &g, const uint8_t *user_tags, uint8_t *tags,
+                                unsigned long long *census, cudaStream_t s);
+cudaError_t launch_gather_tags(const Grid &g, const uint8_t *tags, uint8_t *out, cudaStream_t s);
+
+}  // namespace lbm

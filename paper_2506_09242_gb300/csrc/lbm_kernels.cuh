@@ -1,0 +1,503 @@
+// lbm_kernels.cuh -- kernel templates of the hot path, instantiated once per
+// storage type by lbm_store_*.cu.
+//
+// Layout in HBM: two population arrays A and B of Q planes each, plane i
+// holding h_i = f_i - w_i of every node at offset (z*ny + y)*px + x (x
+// fastest, px = nx rounded up to 32); a byte of tag per node in the same
+// padded order.  One thread owns one node.
+#pragma once
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+constexpr int kStepThreads = 128;
+
+// Host-side conversion of the parameters to the compute type.
+template <typename T> inline KParams<T> make_kparams(int Q, const lbm_params &p)
+{
+    (void)Q;
+    KParams<T> k;
+    k.tau = (T)p.tau;
+    k.omega = (T)(1.0 / p.tau);
+    for (int a = 0; a < 3; ++a) k.force[a] = (T)p.force[a];
+    k.smag18 = (T)(18.0 * p.cs_smag * p.cs_smag);
+    for (int w = 0; w < LBM_NWALLS; ++w)
+        for (int a = 0; a < 3; ++a) k.wall6[w][a] = (T)(6.0 * p.rho_wall * p.wall_u[w][a]);
+    return k;
+}
+
+// Neighbour bookkeeping of one node: the three x positions and nine row
+// offsets (z, y) of its periodic 3x3x3 neighbourhood.
+struct Nbr {
+    int xs[3];      // x-1, x, x+1 (wrapped)
+    int row[3][3];  // row[dy+1][dz+1] = ((z+dz)*ny + (y+dy)) * px (wrapped)
+    int self;
+    __device__ __forceinline__ void init(const Grid &g, int x, int y, int z)
+    {
+        xs[0] = x == 0 ? g.nx - 1 : x - 1;
+        xs[1] = x;
+        xs[2] = x == g.nx - 1 ? 0 : x + 1;
+        const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+        const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+        const int ys[3] = {ym, y, yp};
+        const int zs[3] = {zm, z, zp};
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) row[a][b] = (zs[b] * g.ny + ys[a]) * g.px;
+        self = row[1][1] + x;
+    }
+    // Offset of the node x - c_i (the pull source of direction i).
+    __device__ __forceinline__ int src(int i) const
+    {
+        return row[1 - cvel(i, 1)][1 - cvel(i, 2)] + xs[1 - cvel(i, 0)];
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Fused collide-and-stream (pull, two populations).
+//   GENERAL: tags are read (bounce-back, Ladd walls, forced nodes); without
+//            it every node is a plain fluid node and no tag byte is touched.
+//   CLOSURE: LBM_CLOSURE_BGK, _SMAGORINSKY or _STREAM_ONLY.
+// ---------------------------------------------------------------------------
+template <int Q, typename S, bool GENERAL, int CLOSURE>
+__global__ void __launch_bounds__(kStepThreads)
+    k_collide_stream(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ tags, Grid g,
+                     KParams<typename Store<S>::T> p)
+{
+    using T = typename Store<S>::T;
+    using St = Store<S>;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+
+    Nbr nb;
+    nb.init(g, x, y, z);
+    unsigned t = 0;
+    if (GENERAL) {
+        t = tags[nb.self];
+        if (is_wall_tag(t & kTagMask)) return;  // solid and wall nodes are never updated
+    }
+
+    // Pull: h_i(x) = h*_i(x - c_i).
+    T h[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) h[i] = St::ld(A + (long long)i * g.sN + nb.src(i));
+
+    if (GENERAL && (t & kNearWall)) {
+        // Halfway bounce-back from a SOLID source; Ladd's moving-wall term
+        // 6 w_i rho_wall (c_i . u_wall) from a WALL source.
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const unsigned ts = tags[nb.src(i)] & kTagMask;
+            if (is_wall_tag(ts)) {
+                T v = St::ld(A + (long long)opp(i) * g.sN + nb.self);
+                if (ts >= LBM_TAG_WALL0) {
+                    // select the wall's velocity without indexing the parameter
+                    // block dynamically (which would copy it to local memory)
+                    T ux = T(0), uy = T(0), uz = T(0);
+#pragma unroll
+                    for (int k = 0; k < LBM_NWALLS; ++k)
+                        if (ts == (unsigned)(LBM_TAG_WALL0 + k)) {
+                            ux = p.wall6[k][0];
+                            uy = p.wall6[k][1];
+                            uz = p.wall6[k][2];
+                        }
+                    v += wgt<T>(Q, i) * (T(cvel(i, 0)) * ux + T(cvel(i, 1)) * uy + T(cvel(i, 2)) * uz);
+                }
+                h[i] = v;
+            }
+        }
+    }
+
+    if (CLOSURE != LBM_CLOSURE_STREAM_ONLY) {
+        // Moments of the pulled set: rho = 1 + sum h, j = sum c h.
+        T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            drho += h[i];
+            if (cvel(i, 0)) jx += cvel(i, 0) > 0 ? h[i] : -h[i];
+            if (cvel(i, 1)) jy += cvel(i, 1) > 0 ? h[i] : -h[i];
+            if (cvel(i, 2)) jz += cvel(i, 2) > 0 ? h[i] : -h[i];
+        }
+        const T rho = T(1) + drho;
+        T Gx = T(0), Gy = T(0), Gz = T(0);
+        const bool forced = GENERAL && (t & kTagMask) == LBM_TAG_FORCED;
+        if (forced) {
+            Gx = rho * p.force[0];
+            Gy = rho * p.force[1];
+            Gz = rho * p.force[2];
+            jx += T(0.5) * Gx;
+            jy += T(0.5) * Gy;
+            jz += T(0.5) * Gz;
+        }
+        const T inv = T(1) / rho;
+        const T ux = jx * inv, uy = jy * inv, uz = jz * inv;
+        const T usq15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
+
+        T omega = p.omega;
+        if (CLOSURE == LBM_CLOSURE_SMAGORINSKY) {
+            // Pi^neq_ab = sum c_a c_b (f - f_eq) = sum c_a c_b h - rho u_a u_b
+            //             - (drho / 3) delta_ab   (closed-form equilibrium moments).
+            T sxx = T(0), syy = T(0), szz = T(0), sxy = T(0), sxz = T(0), syz = T(0);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
+                if (cx) sxx += h[i];
+                if (cy) syy += h[i];
+                if (cz) szz += h[i];
+                if (cx * cy) sxy += cx * cy > 0 ? h[i] : -h[i];
+                if (cx * cz) sxz += cx * cz > 0 ? h[i] : -h[i];
+                if (cy * cz) syz += cy * cz > 0 ? h[i] : -h[i];
+            }
+            const T d3 = drho * (T(1) / T(3));
+            const T pxx = sxx - rho * ux * ux - d3, pyy = syy - rho * uy * uy - d3, pzz = szz - rho * uz * uz - d3;
+            const T pxy = sxy - rho * ux * uy, pxz = sxz - rho * ux * uz, pyz = syz - rho * uy * uz;
+            const T pp = pxx * pxx + pyy * pyy + pzz * pzz + T(2) * (pxy * pxy + pxz * pxz + pyz * pyz);
+            const T te = T(0.5) * (p.tau + sqrt(p.tau * p.tau + p.smag18 * sqrt(T(2) * pp) * inv));
+            omega = T(1) / te;
+        }
+
+        const T cf = T(1) - T(0.5) * omega;
+        const T uG = ux * Gx + uy * Gy + uz * Gz;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
+            const T cu = T(cx) * ux + T(cy) * uy + T(cz) * uz;
+            const T w = wgt<T>(Q, i);
+            // h_eq = f_eq - w = w (drho + rho (3 cu + 4.5 cu^2 - 1.5 u^2))
+            const T heq = w * (drho + rho * (cu * (T(3) + T(4.5) * cu) - usq15));
+            T hn = h[i] + omega * (heq - h[i]);
+            if (forced) {
+                // Guo: F_i = w [3 (c - u) + 9 (c.u) c] . G
+                const T cG = T(cx) * Gx + T(cy) * Gy + T(cz) * Gz;
+                hn += cf * w * (T(3) * (cG - uG) + T(9) * cu * cG);
+            }
+            h[i] = hn;
+        }
+    }
+
+#pragma unroll
+    for (int i = 0; i < Q; ++i) St::st(B + (long long)i * g.sN + nb.self, h[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Per-node density and velocity from the stored post-collision set.
+// ---------------------------------------------------------------------------
+template <int Q, typename S>
+__device__ __forceinline__ void node_moments(const S *__restrict__ A, long long sN, int off, bool forced,
+                                             const KParams<typename Store<S>::T> &p, typename Store<S>::T &drho,
+                                             typename Store<S>::T (&u)[3])
+{
+    using T = typename Store<S>::T;
+    T d = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T v = Store<S>::ld(A + (long long)i * sN + off);
+        d += v;
+        if (cvel(i, 0)) jx += cvel(i, 0) > 0 ? v : -v;
+        if (cvel(i, 1)) jy += cvel(i, 1) > 0 ? v : -v;
+        if (cvel(i, 2)) jz += cvel(i, 2) > 0 ? v : -v;
+    }
+    const T rho = T(1) + d;
+    if (forced) {
+        jx -= T(0.5) * rho * p.force[0];
+        jy -= T(0.5) * rho * p.force[1];
+        jz -= T(0.5) * rho * p.force[2];
+    }
+    const T inv = T(1) / rho;
+    drho = d;
+    u[0] = jx * inv;
+    u[1] = jy * inv;
+    u[2] = jz * inv;
+}
+
+template <int Q, typename S, bool GENERAL>
+__global__ void __launch_bounds__(kStepThreads)
+    k_moments(const S *__restrict__ A, const uint8_t *__restrict__ tags, Grid g, KParams<typename Store<S>::T> p,
+              double *__restrict__ rho, double *__restrict__ u)
+{
+    using T = typename Store<S>::T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const int off = (z * g.ny + y) * g.px + x;
+    const long long n = x + (long long)g.nx * (y + (long long)g.ny * z);
+    unsigned t = GENERAL ? (tags[off] & kTagMask) : 0u;
+    if (is_wall_tag(t)) {
+        if (rho) rho[n] = 0.0;
+        if (u) u[n] = u[g.N + n] = u[2 * g.N + n] = 0.0;
+        return;
+    }
+    T d, v[3];
+    node_moments<Q, S>(A, g.sN, off, t == LBM_TAG_FORCED, p, d, v);
+    if (rho) rho[n] = 1.0 + (double)d;
+    if (u) {
+        u[n] = (double)v[0];
+        u[g.N + n] = (double)v[1];
+        u[2 * g.N + n] = (double)v[2];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reduction: FP64 sums over fluid nodes.  Pass 1 writes one partial per block
+// (fixed grid, grid-stride over nodes), pass 2 adds the partials in a fixed
+// order, so the result does not depend on scheduling.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide reduction of kRedSlots values (slot 9 is a max, the rest sums);
+// thread 0 ends with the result in acc.
+__device__ __forceinline__ void block_reduce_slots(double (&acc)[kRedSlots])
+{
+    __shared__ double sm[kRedThreads / 32][kRedSlots];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kRedSlots; ++k) acc[k] = (k == 9) ? warp_max(acc[k]) : warp_sum(acc[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < kRedSlots; ++k) sm[warp][k] = acc[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < kRedSlots; ++k) {
+            double v = lane < kRedThreads / 32 ? sm[lane][k] : (k == 9 ? 0.0 : 0.0);
+            acc[k] = (k == 9) ? warp_max(v) : warp_sum(v);
+        }
+    }
+}
+
+template <int Q, typename S, bool GENERAL>
+__global__ void __launch_bounds__(kRedThreads)
+    k_reduce(const S *__restrict__ A, const uint8_t *__restrict__ tags, Grid g, KParams<typename Store<S>::T> p,
+             double *__restrict__ partials)
+{
+    using T = typename Store<S>::T;
+    double acc[kRedSlots];
+#pragma unroll
+    for (int k = 0; k < kRedSlots; ++k) acc[k] = 0.0;
+    const long long total = (long long)g.nz * g.ny * g.px;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(idx % g.px);
+        if (x >= g.nx) continue;
+        const int off = (int)idx;
+        const unsigned t = GENERAL ? (tags[off] & kTagMask) : 0u;
+        if (is_wall_tag(t)) continue;
+        T d, v[3];
+        node_moments<Q, S>(A, g.sN, off, t == LBM_TAG_FORCED, p, d, v);
+        const double dd = (double)d, rho = 1.0 + dd;
+        const double ux = (double)v[0], uy = (double)v[1], uz = (double)v[2];
+        const double usq = ux * ux + uy * uy + uz * uz;
+        acc[10] += 1.0;
+        if (!isfinite(rho) || !isfinite(usq)) {
+            acc[11] += 1.0;
+            continue;
+        }
+        acc[0] += dd;
+        acc[1] += rho * ux;
+        acc[2] += rho * uy;
+        acc[3] += rho * uz;
+        acc[4] += ux;
+        acc[5] += uy;
+        acc[6] += uz;
+        acc[7] += 0.5 * usq;
+        acc[8] += 0.5 * rho * usq;
+        acc[9] = fmax(acc[9], sqrt(usq));
+    }
+    block_reduce_slots(acc);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < kRedSlots; ++k) partials[(long long)blockIdx.x * kRedSlots + k] = acc[k];
+}
+
+// Second pass: one block adds nblocks partials in a fixed order.
+__global__ void __launch_bounds__(kRedThreads) k_reduce_final(const double *__restrict__ partials, int nblocks,
+                                                             double *__restrict__ out);
+
+// ---------------------------------------------------------------------------
+// Initialisation and population transfer.
+// ---------------------------------------------------------------------------
+template <int Q, typename S>
+__global__ void __launch_bounds__(kStepThreads)
+    k_init(S *__restrict__ A, S *__restrict__ B, Grid g, const double *__restrict__ rho, const double *__restrict__ u)
+{
+    using T = typename Store<S>::T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const int off = (z * g.ny + y) * g.px + x;
+    const long long n = x + (long long)g.nx * (y + (long long)g.ny * z);
+    const double r = rho ? rho[n] : 1.0;
+    const double ux = u ? u[n] : 0.0, uy = u ? u[g.N + n] : 0.0, uz = u ? u[2 * g.N + n] : 0.0;
+    const double usq15 = 1.5 * (ux * ux + uy * uy + uz * uz);
+    const double dr = r - 1.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const double cu = cvel(i, 0) * ux + cvel(i, 1) * uy + cvel(i, 2) * uz;
+        const double heq = wgt<double>(Q, i) * (dr + r * (cu * (3.0 + 4.5 * cu) - usq15));
+        const S v = Store<S>::from_f64(heq);
+        A[(long long)i * g.sN + off] = v;
+        B[(long long)i * g.sN + off] = v;
+    }
+}
+
+template <int Q, typename S>
+__global__ void k_get_pop(const S *__restrict__ A, Grid g, int i, double *__restrict__ f)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const int off = (z * g.ny + y) * g.px + x;
+    const long long n = x + (long long)g.nx * (y + (long long)g.ny * z);
+    double w = 0.0;
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+        if (k == i) w = wgt<double>(Q, k);
+    f[n] = (double)Store<S>::ld(A + (long long)i * g.sN + off) + w;
+}
+
+template <int Q, typename S>
+__global__ void k_set_pop(S *__restrict__ A, S *__restrict__ B, Grid g, int i, const double *__restrict__ f)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const int off = (z * g.ny + y) * g.px + x;
+    const long long n = x + (long long)g.nx * (y + (long long)g.ny * z);
+    double w = 0.0;
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+        if (k == i) w = wgt<double>(Q, k);
+    const S v = Store<S>::from_f64(f[n] - w);
+    A[(long long)i * g.sN + off] = v;
+    B[(long long)i * g.sN + off] = v;
+}
+
+// Block shape shared by the node-per-thread kernels.
+inline void node_launch_shape(const Grid &g, dim3 &grid, dim3 &block)
+{
+    const int bx = g.px >= 128 ? 128 : g.px;  // px is a multiple of 32
+    const int by = kStepThreads / bx;
+    block = dim3(bx, by, 1);
+    grid = dim3((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers, defined once per storage type S by LBM_DEFINE_LAUNCHERS(S).
+// ---------------------------------------------------------------------------
+template <int Q, typename S, bool GEN>
+cudaError_t step_closure(const Launch &L, const KParams<typename Store<S>::T> &kp, dim3 grid, dim3 block)
+{
+    const S *A = (const S *)L.A;
+    S *B = (S *)L.B;
+    switch (L.closure) {
+    case LBM_CLOSURE_BGK: k_collide_stream<Q, S, GEN, LBM_CLOSURE_BGK><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp); break;
+    case LBM_CLOSURE_SMAGORINSKY:
+        k_collide_stream<Q, S, GEN, LBM_CLOSURE_SMAGORINSKY><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp);
+        break;
+    case LBM_CLOSURE_STREAM_ONLY:
+        k_collide_stream<Q, S, GEN, LBM_CLOSURE_STREAM_ONLY><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int Q, typename S> cudaError_t step_q(const Launch &L, const lbm_params &p)
+{
+    dim3 grid, block;
+    node_launch_shape(L.g, grid, block);
+    const auto kp = make_kparams<typename Store<S>::T>(Q, p);
+    return L.general ? step_closure<Q, S, true>(L, kp, grid, block) : step_closure<Q, S, false>(L, kp, grid, block);
+}
+
+template <int Q, typename S>
+cudaError_t reduce_q(const Launch &L, const lbm_params &p, double *partials, int nblocks, double *out)
+{
+    const auto kp = make_kparams<typename Store<S>::T>(Q, p);
+    if (L.general)
+        k_reduce<Q, S, true><<<nblocks, kRedThreads, 0, L.stream>>>((const S *)L.A, L.tags, L.g, kp, partials);
+    else
+        k_reduce<Q, S, false><<<nblocks, kRedThreads, 0, L.stream>>>((const S *)L.A, L.tags, L.g, kp, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_final<<<1, kRedThreads, 0, L.stream>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+template <int Q, typename S> cudaError_t moments_q(const Launch &L, const lbm_params &p, double *rho, double *u)
+{
+    dim3 grid, block;
+    node_launch_shape(L.g, grid, block);
+    const auto kp = make_kparams<typename Store<S>::T>(Q, p);
+    if (L.general)
+        k_moments<Q, S, true><<<grid, block, 0, L.stream>>>((const S *)L.A, L.tags, L.g, kp, rho, u);
+    else
+        k_moments<Q, S, false><<<grid, block, 0, L.stream>>>((const S *)L.A, L.tags, L.g, kp, rho, u);
+    return cudaGetLastError();
+}
+
+#define LBM_DEFINE_LAUNCHERS(S)                                                                              \
+    template <> cudaError_t launch_step<S>(const Launch &L, const lbm_params &p)                             \
+    {                                                                                                        \
+        return L.Q == 19 ? step_q<19, S>(L, p) : step_q<27, S>(L, p);                                       \
+    }                                                                                                        \
+    template <>                                                                                              \
+    cudaError_t launch_reduce<S>(const Launch &L, const lbm_params &p, double *partials, int nb, double *out) \
+    {                                                                                                        \
+        return L.Q == 19 ? reduce_q<19, S>(L, p, partials, nb, out) : reduce_q<27, S>(L, p, partials, nb, out); \
+    }                                                                                                        \
+    template <> cudaError_t launch_moments<S>(const Launch &L, const lbm_params &p, double *rho, double *u)  \
+    {                                                                                                        \
+        return L.Q == 19 ? moments_q<19, S>(L, p, rho, u) : moments_q<27, S>(L, p, rho, u);                 \
+    }                                                                                                        \
+    template <> cudaError_t launch_init<S>(const Launch &L, const double *rho, const double *u)              \
+    {                                                                                                        \
+        dim3 grid, block;                                                                                    \
+        node_launch_shape(L.g, grid, block);                                                                 \
+        if (L.Q == 19)                                                                                       \
+            k_init<19, S><<<grid, block, 0, L.stream>>>((S *)L.A, (S *)L.B, L.g, rho, u);                    \
+        else                                                                                                 \
+            k_init<27, S><<<grid, block, 0, L.stream>>>((S *)L.A, (S *)L.B, L.g, rho, u);                    \
+        return cudaGetLastError();                                                                           \
+    }                                                                                                        \
+    template <> cudaError_t launch_get_pop<S>(const Launch &L, int i, double *f)                             \
+    {                                                                                                        \
+        dim3 grid, block;                                                                                    \
+        node_launch_shape(L.g, grid, block);                                                                 \
+        if (L.Q == 19)                                                                                       \
+            k_get_pop<19, S><<<grid, block, 0, L.stream>>>((const S *)L.A, L.g, i, f);                       \
+        else                                                                                                 \
+            k_get_pop<27, S><<<grid, block, 0, L.stream>>>((const S *)L.A, L.g, i, f);                       \
+        return cudaGetLastError();                                                                           \
+    }                                                                                                        \
+    template <> cudaError_t launch_set_pop<S>(const Launch &L, int i, const double *f)                       \
+    {                                                                                                        \
+        dim3 grid, block;                                                                                    \
+        node_launch_shape(L.g, grid, block);                                                                 \
+        if (L.Q == 19)                                                                                       \
+            k_set_pop<19, S><<<grid, block, 0, L.stream>>>((S *)L.A, (S *)L.B, L.g, i, f);                   \
+        else                                                                                                 \
+            k_set_pop<27, S><<<grid, block, 0, L.stream>>>((S *)L.A, (S *)L.B, L.g, i, f);                   \
+        return cudaGetLastError();                                                                           \
+    }
+
+}  // namespace lbm

@@ -1,0 +1,6 @@
+// Kernel instantiations and launchers for __half population storage.
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+LBM_DEFINE_LAUNCHERS(__half)
+}  // namespace lbm

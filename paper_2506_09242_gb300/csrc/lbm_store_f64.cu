@@ -1,0 +1,6 @@
+// Kernel instantiations and launchers for double population storage.
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+LBM_DEFINE_LAUNCHERS(double)
+}  // namespace lbm

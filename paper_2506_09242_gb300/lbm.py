@@ -1,0 +1,333 @@
+"""Python binding of the C ABI in ``include/lbm.h`` (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``_lib/liblbm.so``; this
+module converts numpy arrays / torch tensors to pointers, passes torch's
+caching allocator and current CUDA stream to the library, and turns status
+codes into exceptions.  There is no CPU fallback: without the compiled
+library, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "_lib" / "liblbm.so"
+
+# Values of include/lbm.h.
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_UNSTABLE, ERR_TIMEOUT = range(7)
+D3Q19, D3Q27 = 19, 27
+F64, F32, F16_SHIFTED, BF16_SHIFTED = 0, 1, 2, 3
+DTYPES = {"f64": F64, "f32": F32, "f16": F16_SHIFTED, "bf16": BF16_SHIFTED}
+TAG_FLUID, TAG_FORCED, TAG_SOLID, TAG_WALL0, NWALLS = 0, 1, 2, 3, 8
+NTAGS = TAG_WALL0 + NWALLS
+CLOSURE_BGK, CLOSURE_SMAGORINSKY, CLOSURE_MLP, CLOSURE_STREAM_ONLY = 0, 1, 2, 3
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_STATE", 5: "ERR_UNSTABLE",
+                6: "ERR_TIMEOUT"}
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class UnstableError(LBMError):
+    """A reduction met a non-finite density or velocity."""
+
+    def __init__(self, status, message, reduction):
+        super().__init__(status, message)
+        self.reduction = reduction
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("tau", ctypes.c_double),
+        ("force", ctypes.c_double * 3),
+        ("closure", ctypes.c_int),
+        ("cs_smag", ctypes.c_double),
+        ("wall_u", (ctypes.c_double * 3) * NWALLS),
+        ("rho_wall", ctypes.c_double),
+    ]
+
+
+class Reduction(ctypes.Structure):
+    _fields_ = [
+        ("mass", ctypes.c_double),
+        ("mom", ctypes.c_double * 3),
+        ("vel", ctypes.c_double * 3),
+        ("ke", ctypes.c_double),
+        ("ke_rho", ctypes.c_double),
+        ("umax", ctypes.c_double),
+        ("n_fluid", ctypes.c_longlong),
+        ("nonfinite", ctypes.c_longlong),
+    ]
+
+    def as_dict(self) -> dict:
+        return {"mass": self.mass, "mom": list(self.mom), "vel": list(self.vel), "ke": self.ke,
+                "ke_rho": self.ke_rho, "umax": self.umax, "n_fluid": self.n_fluid, "nonfinite": self.nonfinite}
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", ctypes.c_void_p)]
+
+
+# name -> (restype, argtypes) of every C ABI entry point.
+_P, _I, _D, _LL, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_size_t
+SIGNATURES = {
+    "lbm_create": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(Allocator), _P, ctypes.POINTER(_P)]),
+    "lbm_destroy": (_I, [_P]),
+    "lbm_set_params": (_I, [_P, ctypes.POINTER(Params)]),
+    "lbm_set_tags": (_I, [_P, _P, _I]),
+    "lbm_get_tags": (_I, [_P, _P, _I]),
+    "lbm_tag_census": (_I, [_P, _P]),
+    "lbm_init_equilibrium": (_I, [_P, _P, _P, _I]),
+    "lbm_step": (_I, [_P, _I]),
+    "lbm_step_count": (_I, [_P, ctypes.POINTER(_LL)]),
+    "lbm_moments": (_I, [_P, _P, _P, _I]),
+    "lbm_reduce": (_I, [_P, ctypes.POINTER(Reduction)]),
+    "lbm_sync": (_I, [_P, _I]),
+    "lbm_get_populations": (_I, [_P, _P, _I]),
+    "lbm_set_populations": (_I, [_P, _P, _I]),
+    "lbm_info": (_I, [_P, ctypes.POINTER(_SZ), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "lbm_last_error": (ctypes.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+def library_path() -> Path:
+    return _LIB_PATH
+
+
+def load():
+    """Loads the compiled library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not _LIB_PATH.exists():
+            raise ImportError(f"CUDA library {_LIB_PATH} is missing: run __graft_entry__.build() first")
+        lib = ctypes.CDLL(str(_LIB_PATH))
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status: int, ctx=None):
+    if status != OK:
+        msg = load().lbm_last_error(ctx).decode(errors="replace")
+        raise LBMError(status, msg)
+
+
+def _buf(a, dtype):
+    """(pointer, on_device, keepalive) for a numpy array or torch tensor."""
+    if a is None:
+        return None, 0, None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != dtype_torch(dtype):
+                raise TypeError(f"expected a {dtype} tensor, got {a.dtype}")
+            if not a.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda), a
+    except ImportError:  # pragma: no cover
+        pass
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(ctypes.c_void_p), 0, arr
+
+
+def dtype_torch(np_dtype):
+    import torch
+    return {np.float64: torch.float64, np.uint8: torch.uint8, np.float32: torch.float32,
+            np.int32: torch.int32}[np.dtype(np_dtype).type]
+
+
+class _TorchAllocator:
+    """Routes the library's device allocations through torch's caching
+    allocator on the given device."""
+
+    def __init__(self, device: int):
+        import torch
+        self.device = device
+        self._torch = torch
+
+        def _alloc(nbytes, stream, user):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), device, stream or 0))
+            except Exception:  # noqa: BLE001 - report as NULL (LBM_ERR_OOM)
+                return None
+
+        def _free(ptr, nbytes, stream, user):
+            if ptr:
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc = ALLOC_FN(_alloc)
+        self._free = FREE_FN(_free)
+        self.struct = Allocator(self._alloc, self._free, None)
+
+
+class Lattice:
+    """One lattice (a library context) on one GPU.
+
+    shape is (nx, ny, nz); fields use numpy order (nz, ny, nx) with x fastest.
+    """
+
+    def __init__(self, nx: int, ny: int, nz: int, lattice: int = D3Q19, dtype="f32", *, device: int = 0,
+                 stream=None, torch_allocator: bool = True):
+        lib = load()
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.Q = int(lattice)
+        self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        self.device = device
+        self._alloc = None
+        stream_handle = None
+        try:
+            import torch
+            if torch.cuda.is_available():
+                torch.cuda.set_device(device)
+                if stream is None:
+                    stream = torch.cuda.current_stream(device)
+                stream_handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+                if torch_allocator:
+                    self._alloc = _TorchAllocator(device)
+        except ImportError:  # pragma: no cover
+            pass
+        self._stream = stream
+        ctx = ctypes.c_void_p()
+        alloc_ptr = ctypes.byref(self._alloc.struct) if self._alloc else None
+        _check(lib.lbm_create(nx, ny, nz, self.Q, self.dtype, alloc_ptr, stream_handle, ctypes.byref(ctx)))
+        self._ctx = ctx
+        self.params = Params()
+        self.params.tau = 1.0
+        self.params.rho_wall = 1.0
+
+    # -- lifetime ------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_ctx", None):
+            load().lbm_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def ctx(self):
+        return self._ctx
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def N(self):
+        return self.nx * self.ny * self.nz
+
+    def _call(self, name, *args):
+        st = getattr(load(), name)(self._ctx, *args)
+        _check(st, self._ctx)
+        return st
+
+    # -- configuration -------------------------------------------------------
+    def set_params(self, tau: float, *, force=(0.0, 0.0, 0.0), closure: int = CLOSURE_BGK, cs_smag: float = 0.0,
+                   wall_u=None, rho_wall: float = 1.0):
+        p = Params()
+        p.tau = tau
+        for a in range(3):
+            p.force[a] = force[a]
+        p.closure = closure
+        p.cs_smag = cs_smag
+        if wall_u is not None:
+            for k, v in enumerate(wall_u):
+                for a in range(3):
+                    p.wall_u[k][a] = v[a]
+        p.rho_wall = rho_wall
+        self._call("lbm_set_params", ctypes.byref(p))
+        self.params = p
+
+    def set_tags(self, tags):
+        ptr, dev, keep = _buf(tags, np.uint8)
+        count = keep.numel() if hasattr(keep, "numel") else keep.size
+        if count != self.N:
+            raise ValueError("tags must have nx*ny*nz entries")
+        self._call("lbm_set_tags", ptr, dev)
+
+    def get_tags(self) -> np.ndarray:
+        out = np.empty(self.shape, dtype=np.uint8)
+        self._call("lbm_get_tags", out.ctypes.data_as(ctypes.c_void_p), 0)
+        return out
+
+    def census(self) -> np.ndarray:
+        out = np.zeros(NTAGS, dtype=np.int64)
+        self._call("lbm_tag_census", out.ctypes.data_as(ctypes.c_void_p))
+        return out
+
+    # -- state -----------------------------------------------------------------
+    def init_equilibrium(self, rho=None, u=None):
+        r, dr, kr = _buf(rho, np.float64)
+        v, dv, kv = _buf(u, np.float64)
+        if rho is not None and u is not None and dr != dv:
+            raise ValueError("rho and u must both be on the host or both on the device")
+        self._call("lbm_init_equilibrium", r, v, dr if rho is not None else dv)
+
+    def step(self, n: int = 1):
+        self._call("lbm_step", int(n))
+
+    def step_count(self) -> int:
+        v = ctypes.c_longlong()
+        self._call("lbm_step_count", ctypes.byref(v))
+        return v.value
+
+    def sync(self, timeout_ms: int = -1):
+        self._call("lbm_sync", int(timeout_ms))
+
+    def moments(self, rho=None, u=None):
+        """Returns (rho, u) as numpy arrays, or fills the given device tensors."""
+        if rho is None and u is None:
+            rho = np.empty(self.shape)
+            u = np.empty((3,) + self.shape)
+        r, dr, _ = _buf(rho, np.float64)
+        v, dv, _ = _buf(u, np.float64)
+        self._call("lbm_moments", r, v, dr if rho is not None else dv)
+        return rho, u
+
+    def reduce(self) -> dict:
+        out = Reduction()
+        st = load().lbm_reduce(self._ctx, ctypes.byref(out))
+        if st == ERR_UNSTABLE:
+            raise UnstableError(st, load().lbm_last_error(self._ctx).decode(), out.as_dict())
+        _check(st, self._ctx)
+        return out.as_dict()
+
+    def get_populations(self, out=None):
+        if out is None:
+            out = np.empty((self.Q,) + self.shape)
+        p, d, _ = _buf(out, np.float64)
+        self._call("lbm_get_populations", p, d)
+        return out
+
+    def set_populations(self, f):
+        p, d, keep = _buf(f, np.float64)
+        self._call("lbm_set_populations", p, d)
+        self._keep = keep
+
+    def info(self) -> dict:
+        nbytes, px, q = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
+        self._call("lbm_info", ctypes.byref(nbytes), ctypes.byref(px), ctypes.byref(q))
+        return {"population_bytes": nbytes.value, "pitch_x": px.value, "Q": q.value}

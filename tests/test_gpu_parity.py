@@ -1,0 +1,391 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances:
+- FP64 storage: max relative population difference <= 1e-12 after 200 steps;
+- FP32 storage: velocity relative L2 <= 1e-5 against the FP64 oracle;
+- FP16 / BF16 shifted storage: one step from a storage-representable state
+  agrees with the oracle's FP64 step rounded to the same type except where
+  FP32 arithmetic flips a rounding: every value within one unit in the last
+  place, and at least 99% of them identical;
+- pure streaming (closure STREAM_ONLY) and tags: bit-exact.
+Sizes span several thread blocks with ragged x, y and z tails.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import lbm_inputs as inp
+import oracle
+from paper_2506_09242_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+
+DT = {"f64": oracle.F64, "f32": oracle.F32, "f16": oracle.F16, "bf16": oracle.BF16}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2506_09242_gb300 import _build
+    _build.build()
+    lbm.load()
+
+
+def make(shape, Q=19, dtype="f64", tags=None, **params):
+    nz, ny, nx = shape
+    lat = lbm.Lattice(nx, ny, nz, Q, dtype)
+    if tags is not None:
+        lat.set_tags(tags)
+    lat.set_params(**params)
+    return lat
+
+
+def oracle_problem(shape, Q=19, tags=None, **params):
+    nz, ny, nx = shape
+    p = dict(params)
+    return oracle.Problem(Q, nx, ny, nz, tags, **p)
+
+
+def max_rel(a, b):
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
+
+
+# ---------------------------------------------------------------------------
+# FP64: populations to 1e-12 relative
+# ---------------------------------------------------------------------------
+def test_f64_tgv2d_config_200_steps():
+    """D3Q19, FP64, periodic 32^3, z-extruded 2D TGV u0 = 0.02, tau = 0.8."""
+    shape = (32, 32, 32)
+    rho, u = inp.tgv2d(32, 32, 32, 0.02)
+    lat = make(shape, tau=0.8)
+    lat.init_equilibrium(rho, u)
+    lat.step(200)
+    f = lat.get_populations()
+    prob = oracle_problem(shape, tau=0.8)
+    g = prob.step(prob.init_equilibrium(rho, u), 200)
+    assert max_rel(f, g) <= 1e-12
+    red = lat.reduce()
+    m0 = float(np.sum(rho))
+    assert abs(red["mass"] - m0) / m0 <= 1e-12
+    ref = prob.reduce(g)
+    assert red["ke"] == pytest.approx(ref["ke"], rel=1e-12)
+    assert lat.step_count() == 200
+    lat.close()
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+@pytest.mark.parametrize("closure", [lbm.CLOSURE_BGK, lbm.CLOSURE_SMAGORINSKY])
+def test_f64_tags_walls_force_ragged(Q, closure):
+    shape = (11, 13, 45)  # nx = 45: one full 32-block and a ragged tail; odd y, z
+    tags = inp.random_tags(shape, seed=9, p_solid=0.15, p_forced=0.3, p_wall=0.06, n_walls=3)
+    walls = [(0.01, 0.0, 0.0), (0.0, -0.02, 0.005), (0.003, 0.004, -0.006)]
+    params = dict(tau=0.62, force=(2e-4, -1e-4, 5e-5), closure=closure, cs_smag=0.17, wall_u=walls)
+    rho, u = inp.random_velocity_field(shape, seed=4, amplitude=0.04)
+    lat = make(shape, Q, "f64", tags, **params)
+    lat.init_equilibrium(rho, u)
+    lat.step(60)
+    f = lat.get_populations()
+    prob = oracle_problem(shape, Q, tags, **params)
+    g = prob.step(prob.init_equilibrium(rho, u), 60)
+    assert max_rel(f, g) <= 1e-12
+    # reductions and moments of the same state
+    red, ref = lat.reduce(), prob.reduce(g)
+    assert red["n_fluid"] == ref["n_fluid"]
+    assert red["mass"] == pytest.approx(ref["mass"], rel=1e-13)
+    for key in ("ke", "ke_rho", "umax"):
+        assert red[key] == pytest.approx(ref[key], rel=1e-11)
+    for a in range(3):
+        assert red["mom"][a] == pytest.approx(ref["mom"][a], rel=1e-10, abs=1e-15)
+        assert red["vel"][a] == pytest.approx(ref["vel"][a], rel=1e-10, abs=1e-15)
+    r_gpu, u_gpu = lat.moments()
+    r_ref, u_ref = prob.moments(g)
+    assert np.max(np.abs(r_gpu - r_ref)) <= 1e-13
+    assert np.max(np.abs(u_gpu - u_ref)) <= 1e-13
+    lat.close()
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_stream_only_is_bit_exact_with_bounce_back(Q):
+    shape = (9, 10, 37)
+    _, w, _ = oracle.lattice(Q)
+    tags = inp.random_tags(shape, seed=3, p_solid=0.2, p_forced=0.0, p_wall=0.0)
+    f0 = inp.random_populations(w, shape, seed=8, amplitude=0.3)
+    lat = make(shape, Q, "f64", tags, tau=1.0, closure=lbm.CLOSURE_STREAM_ONLY)
+    lat.set_populations(f0)
+    # the library stores f - w: use values whose shift is exact in FP64
+    f_in = lat.get_populations()
+    lat.step(3)
+    f = lat.get_populations()
+    prob = oracle_problem(shape, Q, tags, tau=1.0, closure=oracle.STREAM_ONLY)
+    g = prob.step(f_in, 3)
+    assert np.array_equal(f, g)
+    lat.close()
+
+
+def test_tags_roundtrip_census_and_rejection():
+    shape = (7, 9, 33)
+    tags = inp.random_tags(shape, seed=1, p_solid=0.2, p_forced=0.2, p_wall=0.1, n_walls=8)
+    lat = make(shape, tau=0.7)
+    lat.set_tags(tags)
+    assert np.array_equal(lat.get_tags(), tags)
+    assert np.array_equal(lat.census(), np.bincount(tags.ravel(), minlength=lbm.NTAGS))
+    bad = tags.copy()
+    bad[3, 4, 5] = 200
+    with pytest.raises(lbm.LBMError) as e:
+        lat.set_tags(bad)
+    assert e.value.status == lbm.ERR_ARG
+    assert np.array_equal(lat.get_tags(), tags)  # previous tags stay in force
+    dev = torch.from_numpy(tags.ravel()).cuda()
+    lat.set_tags(dev)
+    assert np.array_equal(lat.get_tags(), tags)
+    lat.close()
+
+
+def test_population_roundtrip_and_device_buffers():
+    shape = (5, 6, 40)
+    _, w, _ = oracle.lattice(19)
+    f0 = inp.random_populations(w, shape, seed=2, amplitude=0.1)
+    lat = make(shape, tau=0.9)
+    lat.set_populations(f0)
+    assert max_rel(lat.get_populations(), f0) <= 1e-15
+    dev = torch.empty((19,) + shape, dtype=torch.float64, device="cuda")
+    lat.get_populations(dev)
+    assert max_rel(dev.cpu().numpy(), f0) <= 1e-15
+    rho, u = inp.random_velocity_field(shape, seed=5)
+    lat.init_equilibrium(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    r, v = lat.moments()
+    assert np.max(np.abs(r - rho)) <= 1e-14
+    assert np.max(np.abs(v - u)) <= 1e-14
+    lat.close()
+
+
+# ---------------------------------------------------------------------------
+# FP32: velocity relative L2 <= 1e-5 against the FP64 oracle
+# ---------------------------------------------------------------------------
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_f32_tgv3d_velocity_l2():
+    n, steps = 40, 150
+    rho, u = inp.tgv3d(n, 0.04)
+    tau = 0.53
+    lat = make((n, n, n), 19, "f32", tau=tau)
+    lat.init_equilibrium(rho, u)
+    lat.step(steps)
+    _, ug = lat.moments()
+    prob = oracle_problem((n, n, n), tau=tau)
+    _, ur = prob.moments(prob.step(prob.init_equilibrium(rho, u), steps))
+    assert rel_l2(ug, ur) <= 1e-5
+    lat.close()
+
+
+def test_f32_cavity_velocity_l2():
+    n, steps = 34, 300
+    tags = inp.cavity_tags(n)
+    tau = 3 * 0.1 * (n - 2) / 100.0 + 0.5  # Re = 100 on the interior width
+    params = dict(tau=tau, wall_u=[(0.1, 0.0, 0.0)])
+    lat = make((n, n, n), 19, "f32", tags, **params)
+    lat.init_equilibrium()
+    lat.step(steps)
+    _, ug = lat.moments()
+    prob = oracle_problem((n, n, n), 19, tags, **params)
+    _, ur = prob.moments(prob.step(prob.init_equilibrium(), steps))
+    assert rel_l2(ug, ur) <= 1e-5
+    lat.close()
+
+
+def test_f32_porous_forced_velocity_l2():
+    shape = (24, 24, 48)
+    centres, radii = inp.sphere_list(shape, seed=2506, rmin=2.0, rmax=4.0, count=400)
+    tags, used, por = oracle.spheres(shape, centres, radii, 0.45, pore_tag=oracle.FORCED)
+    params = dict(tau=1.0, force=(1e-5, 0.0, 0.0))
+    lat = make(shape, 19, "f32", tags, **params)
+    lat.init_equilibrium()
+    lat.step(200)
+    _, ug = lat.moments()
+    prob = oracle_problem(shape, 19, tags, **params)
+    _, ur = prob.moments(prob.step(prob.init_equilibrium(), 200))
+    assert rel_l2(ug, ur) <= 1e-5
+    lat.close()
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_f32_smagorinsky_velocity_l2(Q):
+    n, steps = 24, 100
+    rho, u = inp.tgv3d(n, 0.08)
+    params = dict(tau=0.505, closure=lbm.CLOSURE_SMAGORINSKY, cs_smag=0.1)
+    lat = make((n, n, n), Q, "f32", **params)
+    lat.init_equilibrium(rho, u)
+    lat.step(steps)
+    _, ug = lat.moments()
+    prob = oracle_problem((n, n, n), Q, **params)
+    _, ur = prob.moments(prob.step(prob.init_equilibrium(rho, u), steps))
+    assert rel_l2(ug, ur) <= 1e-5
+    lat.close()
+
+
+# ---------------------------------------------------------------------------
+# FP16 / BF16 shifted storage
+# ---------------------------------------------------------------------------
+def ulp(h, kind):
+    mant = 10 if kind == "f16" else 7
+    e = np.floor(np.log2(np.maximum(np.abs(h), 1e-300)))
+    if kind == "f16":
+        e = np.maximum(e, -14)
+    return np.exp2(e - mant)
+
+
+@pytest.mark.parametrize("kind", ["f16", "bf16"])
+@pytest.mark.parametrize("Q", [19, 27])
+def test_half_storage_one_step(kind, Q):
+    shape = (10, 12, 50)
+    _, w, _ = oracle.lattice(Q)
+    tags = inp.random_tags(shape, seed=6, p_solid=0.1, p_forced=0.3, p_wall=0.05, n_walls=2)
+    walls = [(0.02, 0.0, 0.0), (0.0, 0.01, -0.01)]
+    params = dict(tau=0.7, force=(1e-3, 0.0, -5e-4), wall_u=walls)
+    rho, u = inp.random_velocity_field(shape, seed=12, amplitude=0.06)
+    prob = oracle_problem(shape, Q, tags, **params)
+    f0 = oracle.round_storage(prob.init_equilibrium(rho, u), DT[kind])
+    lat = make(shape, Q, kind, tags, **params)
+    lat.set_populations(f0)
+    assert np.array_equal(lat.get_populations(), f0)  # representable state round-trips exactly
+    lat.step(1)
+    f = lat.get_populations()
+    g = oracle.round_storage(prob.step(f0, 1), DT[kind])
+    wv = w.reshape(-1, 1, 1, 1)
+    hg, hr = f - wv, g - wv
+    diff = np.abs(hg - hr)
+    assert np.all(diff <= ulp(hr, kind) * 1.0000001)
+    assert np.mean(diff == 0) >= 0.99
+    lat.close()
+
+
+@pytest.mark.parametrize("kind", ["f16", "bf16"])
+def test_half_storage_error_after_200_steps_is_bounded(kind):
+    """Error statement (not bit parity): 2D TGV config at 32^3 after 200 steps,
+    velocity relative L2 against the FP64 oracle; the bound is a sanity limit."""
+    n = 32
+    rho, u = inp.tgv2d(n, n, n, 0.02)
+    lat = make((n, n, n), 19, kind, tau=0.8)
+    lat.init_equilibrium(rho, u)
+    lat.step(200)
+    _, ug = lat.moments()
+    prob = oracle_problem((n, n, n), tau=0.8)
+    _, ur = prob.moments(prob.step(prob.init_equilibrium(rho, u), 200))
+    err = rel_l2(ug, ur)
+    print(f"{kind}: velocity rel L2 after 200 steps = {err:.3e}")
+    assert err <= (0.5 if kind == "bf16" else 5e-2)
+    lat.close()
+
+
+# ---------------------------------------------------------------------------
+# Failure paths (no GPU fault: host-side checks and bounded waits)
+# ---------------------------------------------------------------------------
+def test_nan_injection_reports_unstable():
+    shape = (6, 6, 32)
+    _, w, _ = oracle.lattice(19)
+    f0 = inp.random_populations(w, shape, seed=2)
+    f0[3, 2, 3, 7] = np.nan
+    lat = make(shape, tau=0.8)
+    lat.set_populations(f0)
+    with pytest.raises(lbm.UnstableError) as e:
+        lat.reduce()
+    assert e.value.status == lbm.ERR_UNSTABLE
+    assert e.value.reduction["nonfinite"] == 1
+    assert e.value.reduction["n_fluid"] == 6 * 6 * 32
+    lat.close()
+
+
+def test_bad_params_rejected():
+    lat = make((4, 4, 32), tau=0.8)
+    for kw in (dict(tau=0.5), dict(tau=float("nan")), dict(tau=0.7, closure=9), dict(tau=0.7, cs_smag=-1.0)):
+        with pytest.raises(lbm.LBMError) as e:
+            lat.set_params(**kw)
+        assert e.value.status == lbm.ERR_ARG
+    with pytest.raises(lbm.LBMError):
+        lat.step(-1)
+    lat.close()
+
+
+def test_sync_timeout_is_bounded():
+    lat = make((4, 4, 32), tau=0.8)
+    torch.cuda._sleep(int(2e8))  # a bounded busy kernel on the same stream
+    with pytest.raises(lbm.LBMError) as e:
+        lat.sync(timeout_ms=1)
+    assert e.value.status == lbm.ERR_TIMEOUT
+    lat.sync(timeout_ms=60000)
+    lat.close()
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads in the benchmark's launch configuration: sampled nodes
+# against the oracle, computed node by node from their 3x3x3 neighbourhood.
+# ---------------------------------------------------------------------------
+def _neighbourhood(field, z, y, x):
+    idx = [np.arange(v - 1, v + 2) % field.shape[-3 + k] for k, v in enumerate((z, y, x))]
+    return field[..., idx[0][:, None, None], idx[1][None, :, None], idx[2][None, None, :]]
+
+
+def _sampled_check(lat, Q, kind, rho, u, tags, params, cells):
+    """One step from an equilibrium state; compares sampled nodes with an
+    oracle step of their periodic 3x3x3 neighbourhood (the centre node of a
+    3^3 periodic block sees exactly its true neighbours)."""
+    N = lat.N
+    out = torch.empty((Q, N), dtype=torch.float64, device="cuda")
+    lat.get_populations(out)
+    z, y, x = cells.T
+    flat = torch.from_numpy(x + lat.nx * (y + lat.ny * z)).cuda()
+    got = out[:, flat].cpu().numpy()
+    del out
+    torch.cuda.empty_cache()
+    maxdiff = 0.0
+    _, w, _ = oracle.lattice(Q)
+    for k, (cz, cy, cx) in enumerate(cells):
+        r = _neighbourhood(rho, cz, cy, cx) if rho is not None else np.ones((3, 3, 3))
+        v = _neighbourhood(u, cz, cy, cx) if u is not None else np.zeros((3, 3, 3, 3))
+        t = _neighbourhood(tags, cz, cy, cx) if tags is not None else None
+        prob = oracle.Problem(Q, 3, 3, 3, t, **params)
+        f0 = oracle.round_storage(prob.init_equilibrium(r, v), DT[kind])
+        g = prob.step(f0, 1)[:, 1, 1, 1]
+        maxdiff = max(maxdiff, float(np.max(np.abs(got[:, k] - g))))
+    return maxdiff
+
+
+def test_full_size_tgv512_f32_sampled():
+    n = 512
+    rho, u = inp.tgv3d(n, 0.04)
+    tau = 0.5 + 3 * 0.04 * (n / (2 * math.pi)) / 1600.0
+    lat = make((n, n, n), 19, "f32", tau=tau)
+    lat.init_equilibrium(rho, u)
+    m0 = lat.reduce()["mass"]
+    lat.step(1)
+    rng = np.random.default_rng(0)
+    cells = np.stack([rng.integers(0, n, 48), rng.integers(0, n, 48), rng.integers(0, n, 48)], axis=1)
+    cells = np.vstack([cells, [[0, 0, 0], [n - 1, n - 1, n - 1], [0, n - 1, 0], [n - 1, 0, n - 1]]])
+    d = _sampled_check(lat, 19, "f32", rho, u, None, dict(tau=tau), cells)
+    assert d <= 1e-7  # FP32 arithmetic on |h| <= ~0.1
+    lat.step(9)
+    red = lat.reduce()
+    assert abs(red["mass"] - m0) / m0 <= 1e-6
+    assert max(abs(v) for v in red["mom"]) <= 1e-6 * n ** 3 * 0.04
+    lat.close()
+
+
+def test_full_size_cavity256_f32_sampled():
+    n = 256
+    tags = inp.cavity_tags(n)
+    tau = 3 * 0.1 * n / 1000.0 + 0.5
+    params = dict(tau=tau, wall_u=[(0.1, 0.0, 0.0)])
+    lat = make((n, n, n), 19, "f32", tags, **params)
+    lat.init_equilibrium()
+    lat.step(1)
+    rng = np.random.default_rng(1)
+    cells = np.stack([np.full(32, n - 2), rng.integers(1, n - 1, 32), rng.integers(1, n - 1, 32)], axis=1)
+    cells = np.vstack([cells, [[n - 2, 1, 1], [n - 2, n - 2, n - 2], [1, 1, 1], [n // 2, n // 2, n // 2]]])
+    d = _sampled_check(lat, 19, "f32", None, None, tags, params, cells)
+    assert d <= 1e-7
+    lat.close()
