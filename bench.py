@@ -335,7 +335,7 @@ def run_ours(args):
             dist.barrier()
 
     lat, fields, desc = make_workload(args.workload, args.dtype)
-    Q = int(desc["lattice"][4:])
+    Q = int(desc["lattice"][3:])
     cells = lat.N
     sampler = ClockSampler(local)
     sampler.start()
@@ -371,7 +371,7 @@ def run_ours(args):
                 continue
             v, _, d = make_workload(wl, dt)
             tms, kms, _ = time_lattice(v, 5, 3, args.inner)
-            q = int(d["lattice"][4:])
+            q = int(d["lattice"][3:])
             ach = 2 * q * SIZE[dt] * v.N / (kms * 1e-3) / 1e9
             variants[d["workload"]] = {"glups": v.N * args.inner * 5 / (tms * 1e-3) / 1e9,
                                        "kernel_gbs": ach, "frac_of_peak": ach / peak}

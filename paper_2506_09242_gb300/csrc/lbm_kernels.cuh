@@ -281,15 +281,37 @@ __device__ __forceinline__ void block_reduce_slots(double (&acc)[kRedSlots])
     }
 }
 
+// Per-thread accumulator of the reduction: plain FP64 for FP64 compute; for
+// FP32 compute a double-float pair (hi + lo) updated with Knuth's TwoSum,
+// which keeps about 44 significant bits while staying off the FP64 pipe
+// (GB300 has a low FP64 rate); partials are combined in FP64.
+template <typename T> struct Acc {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ double get() const { return v; }
+};
+template <> struct Acc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float s = hi + x;
+        const float bp = s - hi;
+        const float e = (hi - (s - bp)) + (x - bp);
+        hi = s;
+        lo += e;
+    }
+    __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+};
+
 template <int Q, typename S, bool GENERAL>
 __global__ void __launch_bounds__(kRedThreads)
     k_reduce(const S *__restrict__ A, const uint8_t *__restrict__ tags, Grid g, KParams<typename Store<S>::T> p,
              double *__restrict__ partials)
 {
     using T = typename Store<S>::T;
-    double acc[kRedSlots];
-#pragma unroll
-    for (int k = 0; k < kRedSlots; ++k) acc[k] = 0.0;
+    Acc<T> a_dm, a_m[3], a_v[3], a_ke, a_ker;
+    T usq_max = T(0);
+    unsigned n_fluid = 0, n_bad = 0;
     const long long total = (long long)g.nz * g.ny * g.px;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -300,25 +322,26 @@ __global__ void __launch_bounds__(kRedThreads)
         if (is_wall_tag(t)) continue;
         T d, v[3];
         node_moments<Q, S>(A, g.sN, off, t == LBM_TAG_FORCED, p, d, v);
-        const double dd = (double)d, rho = 1.0 + dd;
-        const double ux = (double)v[0], uy = (double)v[1], uz = (double)v[2];
-        const double usq = ux * ux + uy * uy + uz * uz;
-        acc[10] += 1.0;
+        const T rho = T(1) + d;
+        const T usq = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        ++n_fluid;
         if (!isfinite(rho) || !isfinite(usq)) {
-            acc[11] += 1.0;
+            ++n_bad;
             continue;
         }
-        acc[0] += dd;
-        acc[1] += rho * ux;
-        acc[2] += rho * uy;
-        acc[3] += rho * uz;
-        acc[4] += ux;
-        acc[5] += uy;
-        acc[6] += uz;
-        acc[7] += 0.5 * usq;
-        acc[8] += 0.5 * rho * usq;
-        acc[9] = fmax(acc[9], sqrt(usq));
+        a_dm.add(d);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            a_m[k].add(rho * v[k]);
+            a_v[k].add(v[k]);
+        }
+        a_ke.add(T(0.5) * usq);
+        a_ker.add(T(0.5) * rho * usq);
+        usq_max = usq > usq_max ? usq : usq_max;
     }
+    double acc[kRedSlots] = {a_dm.get(),  a_m[0].get(),         a_m[1].get(),         a_m[2].get(),
+                             a_v[0].get(), a_v[1].get(),         a_v[2].get(),         a_ke.get(),
+                             a_ker.get(),  sqrt((double)usq_max), (double)n_fluid, (double)n_bad};
     block_reduce_slots(acc);
     if (threadIdx.x == 0)
 #pragma unroll
@@ -336,6 +359,7 @@ template <int Q, typename S>
 __global__ void __launch_bounds__(kStepThreads)
     k_init(S *__restrict__ A, S *__restrict__ B, Grid g, const double *__restrict__ rho, const double *__restrict__ u)
 {
+    // h_eq in the compute type (FP32 except for FP64 storage).
     using T = typename Store<S>::T;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -343,15 +367,16 @@ __global__ void __launch_bounds__(kStepThreads)
     if (x >= g.nx || y >= g.ny) return;
     const int off = (z * g.ny + y) * g.px + x;
     const long long n = x + (long long)g.nx * (y + (long long)g.ny * z);
-    const double r = rho ? rho[n] : 1.0;
-    const double ux = u ? u[n] : 0.0, uy = u ? u[g.N + n] : 0.0, uz = u ? u[2 * g.N + n] : 0.0;
-    const double usq15 = 1.5 * (ux * ux + uy * uy + uz * uz);
-    const double dr = r - 1.0;
+    const T dr = rho ? (T)(rho[n] - 1.0) : T(0);
+    const T r = T(1) + dr;
+    const T ux = u ? (T)u[n] : T(0), uy = u ? (T)u[g.N + n] : T(0), uz = u ? (T)u[2 * g.N + n] : T(0);
+    const T usq15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const double cu = cvel(i, 0) * ux + cvel(i, 1) * uy + cvel(i, 2) * uz;
-        const double heq = wgt<double>(Q, i) * (dr + r * (cu * (3.0 + 4.5 * cu) - usq15));
-        const S v = Store<S>::from_f64(heq);
+        const T cu = T(cvel(i, 0)) * ux + T(cvel(i, 1)) * uy + T(cvel(i, 2)) * uz;
+        const T heq = wgt<T>(Q, i) * (dr + r * (cu * (T(3) + T(4.5) * cu) - usq15));
+        S v;
+        Store<S>::st(&v, heq);
         A[(long long)i * g.sN + off] = v;
         B[(long long)i * g.sN + off] = v;
     }

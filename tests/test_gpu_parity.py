@@ -6,7 +6,9 @@ Tolerances:
 - FP16 / BF16 shifted storage: one step from a storage-representable state
   agrees with the oracle's FP64 step rounded to the same type except where
   FP32 arithmetic flips a rounding: every value within one unit in the last
-  place, and at least 99% of them identical;
+  place of the storage type plus the absolute FP32 arithmetic error on the
+  O(0.1) intermediates (1e-8, which matters only for values near zero, where
+  a BF16 ulp is tiny), and at least 99% of them identical;
 - pure streaming (closure STREAM_ONLY) and tags: bit-exact.
 Sizes span several thread blocks with ragged x, y and z tails.
 """
@@ -259,7 +261,8 @@ def test_half_storage_one_step(kind, Q):
     wv = w.reshape(-1, 1, 1, 1)
     hg, hr = f - wv, g - wv
     diff = np.abs(hg - hr)
-    assert np.all(diff <= ulp(hr, kind) * 1.0000001)
+    excess = diff - (ulp(hr, kind) * 1.0000001 + 1e-8)
+    assert np.all(excess <= 0), f"worst excess {excess.max():.3e} at |h| = {abs(hr.ravel()[excess.argmax()]):.3e}"
     assert np.mean(diff == 0) >= 0.99
     lat.close()
 
