@@ -192,6 +192,36 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device);
  * number of populations.  Any pointer may be NULL. */
 lbm_status lbm_info(lbm_ctx *ctx, size_t *population_bytes, int *pitch_x, int *q);
 
+/* Largest lattice lbm_reduce_noalloc accepts (32-bit node offsets). */
+#define LBM_NOALLOC_MAX_NODES 2147483647LL
+
+/* Domain reduction that allocates no memory (the paper has no counterpart;
+ * it exists for callers that cannot allocate device memory: a host code that
+ * owns the whole GPU through its own memory pool and forbids other
+ * allocations, such as an analysis plug-in inside another solver, or a time
+ * loop that cannot afford the device synchronisation of cudaMalloc).
+ *
+ * Computes the same sums as lbm_reduce, without a context, over populations
+ * the caller already holds on the device:
+ *  h       device array of offset-stripped populations h_i = f_i - w_i in the
+ *          storage type of dtype, layout [Q][nz][ny][nx] (x fastest, no
+ *          padding, plane stride nx*ny*nz);
+ *  tags    device array of nx*ny*nz tags (values < LBM_NTAGS), or NULL for
+ *          all fluid;
+ *  params  only params->force is read (for FORCED nodes); may be NULL;
+ *  stream  cudaStream_t to run on (NULL: legacy default stream);
+ *  out     host struct, filled on LBM_OK and on LBM_ERR_UNSTABLE.
+ * Scratch: the per-block partials live in a file-scope device array of
+ * 117,888 bytes that every GPU loading the library holds until exit; calls
+ * never call cudaMalloc, cudaFree or any allocating routine.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress), so
+ * that first call should come before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU race and must be serialised by the
+ * caller.  Synchronizes the stream.  Errors: ARG (NULL pointer, bad enum,
+ * a size < 1, more than LBM_NOALLOC_MAX_NODES nodes), CUDA, UNSTABLE. */
+lbm_status lbm_reduce_noalloc(const void *h, lbm_lattice lattice, lbm_dtype dtype, int nx, int ny, int nz,
+                              const uint8_t *tags, const lbm_params *params, void *stream, lbm_reduction *out);
+
 /* Text of the last failure of ctx (or of a call without a context, for
  * ctx == NULL).  Never NULL; valid until the next call on the same ctx. */
 const char *lbm_last_error(const lbm_ctx *ctx);

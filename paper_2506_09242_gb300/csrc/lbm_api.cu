@@ -156,6 +156,12 @@ bool valid_params(const lbm_params *p, std::string &why)
 
 }  // namespace
 
+namespace lbm {
+// Lets entry points without a context (lbm_noalloc.cu) report through
+// lbm_last_error(NULL).
+void set_last_error_global(const char *msg) { g_err = msg; }
+}  // namespace lbm
+
 // ---------------------------------------------------------------------------
 // Storage-independent kernels.
 // ---------------------------------------------------------------------------

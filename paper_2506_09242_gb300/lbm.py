@@ -96,6 +96,7 @@ SIGNATURES = {
     "lbm_set_populations": (_I, [_P, _P, _I]),
     "lbm_info": (_I, [_P, ctypes.POINTER(_SZ), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "lbm_last_error": (ctypes.c_char_p, [_P]),
+    "lbm_reduce_noalloc": (_I, [_P, _I, _I, _I, _I, _I, _P, ctypes.POINTER(Params), _P, ctypes.POINTER(Reduction)]),
 }
 
 _lib = None
@@ -331,3 +332,31 @@ class Lattice:
         nbytes, px, q = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
         self._call("lbm_info", ctypes.byref(nbytes), ctypes.byref(px), ctypes.byref(q))
         return {"population_bytes": nbytes.value, "pitch_x": px.value, "Q": q.value}
+
+
+def reduce_noalloc(h, Q: int, dtype, nx: int, ny: int, nz: int, tags=None, force=(0.0, 0.0, 0.0), stream=None):
+    """Domain reduction over caller-held device populations without any device
+    allocation (``lbm_reduce_noalloc``).  ``h``: CUDA tensor of h = f - w in
+    the storage type, shape (Q, nz, ny, nx); ``tags``: CUDA uint8 tensor or
+    None."""
+    import torch
+    lib = load()
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    if not (isinstance(h, torch.Tensor) and h.is_cuda and h.is_contiguous()):
+        raise TypeError("h must be a contiguous CUDA tensor")
+    if tags is not None and not (isinstance(tags, torch.Tensor) and tags.is_cuda and tags.dtype == torch.uint8):
+        raise TypeError("tags must be a CUDA uint8 tensor")
+    p = Params()
+    for a in range(3):
+        p.force[a] = force[a]
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    out = Reduction()
+    st = lib.lbm_reduce_noalloc(ctypes.c_void_p(h.data_ptr()), Q, dt, nx, ny, nz,
+                                ctypes.c_void_p(tags.data_ptr()) if tags is not None else None,
+                                ctypes.byref(p), handle, ctypes.byref(out))
+    if st == ERR_UNSTABLE:
+        raise UnstableError(st, lib.lbm_last_error(None).decode(), out.as_dict())
+    _check(st, None)
+    return out.as_dict()
