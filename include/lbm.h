@@ -188,6 +188,27 @@ lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int on_device);
  * Does not reset the step counter.  Asynchronous for device inputs. */
 lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device);
 
+/* Random overlapping spheres as a porous medium: the synthetic stand-in for
+ * the Berea sandstone volume of Sec. 3.3.  centres[n][3] (host, integer node
+ * coordinates, any value: wrapped periodically) and radii[n] (host, in
+ * [0, 1024]) are taken in order; a node is solid when, for some sphere, the
+ * squared periodic minimum-image distance to its centre (an integer,
+ * compared as a double) is <= r*r.  Spheres are added until the pore
+ * fraction is <= target_porosity, checked before each sphere, or the list
+ * ends.  Solid nodes get LBM_TAG_SOLID, the others pore_tag (FLUID or
+ * FORCED); the tags are then installed as by lbm_set_tags.  *n_used and
+ * *porosity (either may be NULL) receive the number of spheres used and the
+ * final pore fraction.  Synchronizes.  Errors: ARG, OOM, CUDA. */
+lbm_status lbm_geometry_spheres(lbm_ctx *ctx, const int32_t *centres, const double *radii, int n_spheres,
+                                double target_porosity, uint8_t pore_tag, int *n_used, double *porosity);
+
+/* Enstrophy average over all N nodes (Sec. 3.1): (1/N) sum |w|^2 / 2 with
+ * w = curl u and u from lbm_moments (0 on solid and wall nodes), each
+ * derivative the eighth-order centred difference with weights 4/5, -1/5,
+ * 4/105, -1/280, periodic in every direction.  Arithmetic in FP64 for FP64
+ * storage, FP32 otherwise, accumulated in FP64.  Synchronizes. */
+lbm_status lbm_enstrophy(lbm_ctx *ctx, double *out);
+
 /* Library-side sizes: bytes of one population array, x pitch in nodes,
  * number of populations.  Any pointer may be NULL. */
 lbm_status lbm_info(lbm_ctx *ctx, size_t *population_bytes, int *pitch_x, int *q);

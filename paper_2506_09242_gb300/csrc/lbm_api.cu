@@ -10,6 +10,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <vector>
 
 #include "lbm_kernels.cuh"
 
@@ -549,6 +550,82 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device)
                  "population scatter");
     }
     return on_device ? LBM_OK : sync(ctx);
+}
+
+lbm_status lbm_geometry_spheres(lbm_ctx *ctx, const int32_t *centres, const double *radii, int n_spheres,
+                                double target_porosity, uint8_t pore_tag, int *n_used, double *porosity)
+{
+    if (!ctx) return fail(ctx, LBM_ERR_ARG, "NULL context");
+    if (n_spheres < 0 || (n_spheres > 0 && (!centres || !radii))) return fail(ctx, LBM_ERR_ARG, "bad sphere list");
+    if (pore_tag != LBM_TAG_FLUID && pore_tag != LBM_TAG_FORCED)
+        return fail(ctx, LBM_ERR_ARG, "pore_tag must be LBM_TAG_FLUID or LBM_TAG_FORCED");
+    if (!isfinite(target_porosity)) return fail(ctx, LBM_ERR_ARG, "target porosity must be finite");
+    for (int s = 0; s < n_spheres; ++s)
+        if (!(radii[s] >= 0.0) || !(radii[s] <= 1024.0)) return fail(ctx, LBM_ERR_ARG, "radius %d not in [0, 1024]", s);
+    const long long N = ctx->g.N;
+    const size_t ns = (size_t)n_spheres;
+    Tmp dc(ctx, 3 * sizeof(int32_t) * ns), dr(ctx, sizeof(double) * ns), cover(ctx, sizeof(uint32_t) * (size_t)N),
+        count(ctx, sizeof(uint32_t) * (ns + 1)), tags(ctx, (size_t)N);
+    if ((ns && (!dc.p || !dr.p)) || !cover.p || !count.p || !tags.p)
+        return fail(ctx, LBM_ERR_OOM, "geometry staging allocation failed");
+    if (ns) {
+        CUDA_TRY(ctx, cudaMemcpyAsync(dc.p, centres, 3 * sizeof(int32_t) * ns, cudaMemcpyHostToDevice, ctx->stream), "centres");
+        CUDA_TRY(ctx, cudaMemcpyAsync(dr.p, radii, sizeof(double) * ns, cudaMemcpyHostToDevice, ctx->stream), "radii");
+    }
+    CUDA_TRY(ctx, cudaMemsetAsync(cover.p, 0xff, sizeof(uint32_t) * (size_t)N, ctx->stream), "cover reset");
+    CUDA_TRY(ctx, cudaMemsetAsync(count.p, 0, sizeof(uint32_t) * (ns + 1), ctx->stream), "count reset");
+    CUDA_TRY(ctx, launch_sphere_cover(ctx->nx, ctx->ny, ctx->nz, (const int *)dc.p, (const double *)dr.p, n_spheres,
+                                      (uint32_t *)cover.p, ctx->stream),
+             "sphere cover");
+    CUDA_TRY(ctx, launch_sphere_histogram(N, (const uint32_t *)cover.p, (uint32_t *)count.p, ctx->stream), "histogram");
+    std::vector<uint32_t> hist(ns + 1);
+    CUDA_TRY(ctx, cudaMemcpyAsync(hist.data(), count.p, sizeof(uint32_t) * (ns + 1), cudaMemcpyDeviceToHost, ctx->stream),
+             "histogram copy");
+    lbm_status st = sync(ctx);
+    if (st != LBM_OK) return st;
+    // Sequential stopping rule: before adding sphere s, stop if the pore
+    // fraction is already at or below the target.
+    long long solid = 0;
+    int used = n_spheres;
+    for (int s = 0; s < n_spheres; ++s) {
+        if ((double)(N - solid) / (double)N <= target_porosity) {
+            used = s;
+            break;
+        }
+        solid += hist[s];
+    }
+    CUDA_TRY(ctx, launch_sphere_tags(N, (const uint32_t *)cover.p, (uint32_t)used, pore_tag, (uint8_t *)tags.p, ctx->stream),
+             "sphere tags");
+    st = lbm_set_tags(ctx, (const uint8_t *)tags.p, 1);
+    if (st != LBM_OK) return st;
+    if (n_used) *n_used = used;
+    if (porosity) *porosity = (double)(N - solid) / (double)N;
+    return LBM_OK;
+}
+
+lbm_status lbm_enstrophy(lbm_ctx *ctx, double *out)
+{
+    if (!ctx || !out) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    const long long N = ctx->g.N;
+    Tmp u(ctx, 3 * sizeof(double) * (size_t)N);
+    if (!u.p) return fail(ctx, LBM_ERR_OOM, "velocity staging allocation failed");
+    Launch L = make_launch(ctx);
+    CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
+                 using S = std::remove_pointer_t<decltype(tag)>;
+                 return launch_moments<S>(L, ctx->params, nullptr, (double *)u.p);
+             }),
+             "moments");
+    long long nb = (N + kRedThreads - 1) / kRedThreads;
+    if (nb > kRedBlocks) nb = kRedBlocks;
+    CUDA_TRY(ctx, launch_enstrophy(ctx->dtype == LBM_F64, ctx->nx, ctx->ny, ctx->nz, (const double *)u.p, ctx->partials,
+                                   (int)nb, ctx->red_out, ctx->stream),
+             "enstrophy");
+    double r[kRedSlots];
+    CUDA_TRY(ctx, cudaMemcpyAsync(r, ctx->red_out, sizeof r, cudaMemcpyDeviceToHost, ctx->stream), "enstrophy copy");
+    lbm_status st = sync(ctx);
+    if (st != LBM_OK) return st;
+    *out = r[0] / (double)N;
+    return LBM_OK;
 }
 
 lbm_status lbm_info(lbm_ctx *ctx, size_t *population_bytes, int *pitch_x, int *q)

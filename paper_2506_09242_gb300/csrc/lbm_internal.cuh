@@ -138,4 +138,13 @@ cudaError_t launch_prepare_tags(int Q, const Grid &g, const uint8_t *user_tags, 
                                 unsigned long long *census, cudaStream_t s);
 cudaError_t launch_gather_tags(const Grid &g, const uint8_t *tags, uint8_t *out, cudaStream_t s);
 
+// Porous-medium generator and enstrophy diagnostic (lbm_diag.cu).
+cudaError_t launch_sphere_cover(int nx, int ny, int nz, const int *centres, const double *radii, int n,
+                                uint32_t *cover, cudaStream_t s);
+cudaError_t launch_sphere_histogram(long long N, const uint32_t *cover, uint32_t *count, cudaStream_t s);
+cudaError_t launch_sphere_tags(long long N, const uint32_t *cover, uint32_t used, uint8_t pore_tag, uint8_t *tags,
+                               cudaStream_t s);
+cudaError_t launch_enstrophy(bool fp64, int nx, int ny, int nz, const double *u, double *partials, int nblocks,
+                             double *out, cudaStream_t s);
+
 }  // namespace lbm

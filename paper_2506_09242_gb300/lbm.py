@@ -96,6 +96,8 @@ SIGNATURES = {
     "lbm_set_populations": (_I, [_P, _P, _I]),
     "lbm_info": (_I, [_P, ctypes.POINTER(_SZ), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "lbm_last_error": (ctypes.c_char_p, [_P]),
+    "lbm_geometry_spheres": (_I, [_P, _P, _P, _I, _D, ctypes.c_uint8, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "lbm_enstrophy": (_I, [_P, ctypes.POINTER(_D)]),
     "lbm_reduce_noalloc": (_I, [_P, _I, _I, _I, _I, _I, _P, ctypes.POINTER(Params), _P, ctypes.POINTER(Reduction)]),
 }
 
@@ -327,6 +329,22 @@ class Lattice:
         p, d, keep = _buf(f, np.float64)
         self._call("lbm_set_populations", p, d)
         self._keep = keep
+
+    def geometry_spheres(self, centres, radii, target_porosity: float, pore_tag: int = TAG_FLUID):
+        """Random-sphere medium; returns (n_used, porosity)."""
+        c = np.ascontiguousarray(centres, dtype=np.int32)
+        r = np.ascontiguousarray(radii, dtype=np.float64)
+        if c.shape != (len(r), 3):
+            raise ValueError("centres must have shape (n, 3)")
+        used, por = ctypes.c_int(), ctypes.c_double()
+        self._call("lbm_geometry_spheres", c.ctypes.data_as(ctypes.c_void_p), r.ctypes.data_as(ctypes.c_void_p),
+                   len(r), float(target_porosity), int(pore_tag), ctypes.byref(used), ctypes.byref(por))
+        return used.value, por.value
+
+    def enstrophy(self) -> float:
+        out = ctypes.c_double()
+        self._call("lbm_enstrophy", ctypes.byref(out))
+        return out.value
 
     def info(self) -> dict:
         nbytes, px, q = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
