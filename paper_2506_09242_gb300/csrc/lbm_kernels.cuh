@@ -56,7 +56,115 @@ struct Nbr {
 };
 
 // ---------------------------------------------------------------------------
-// Fused collide-and-stream (pull, two populations).
+// Boundary rules for one fluid node next to a wall (tag bit kNearWall):
+// halfway bounce-back from a SOLID source, h_i(x) = h*_opp(i)(x); Ladd's
+// moving-wall term from a WALL_k source, + 6 w_i rho_wall (c_i . u_wall_k).
+// ---------------------------------------------------------------------------
+template <int Q, typename S>
+__device__ __forceinline__ void apply_walls(typename Store<S>::T (&h)[Q], const S *__restrict__ A,
+                                            const uint8_t *__restrict__ tags, const Grid &g, const Nbr &nb,
+                                            const KParams<typename Store<S>::T> &p)
+{
+    using T = typename Store<S>::T;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const unsigned ts = tags[nb.src(i)] & kTagMask;
+        if (is_wall_tag(ts)) {
+            T v = Store<S>::ld(A + (long long)opp(i) * g.sN + nb.self);
+            if (ts >= LBM_TAG_WALL0) {
+                // select the wall's velocity without indexing the parameter
+                // block dynamically (which would copy it to local memory)
+                T ux = T(0), uy = T(0), uz = T(0);
+#pragma unroll
+                for (int k = 0; k < LBM_NWALLS; ++k)
+                    if (ts == (unsigned)(LBM_TAG_WALL0 + k)) {
+                        ux = p.wall6[k][0];
+                        uy = p.wall6[k][1];
+                        uz = p.wall6[k][2];
+                    }
+                v += wgt<T>(Q, i) * (T(cvel(i, 0)) * ux + T(cvel(i, 1)) * uy + T(cvel(i, 2)) * uz);
+            }
+            h[i] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Collision of one node's pulled set (in place), Sec. 3.1 BGK with the
+// second-order weighted equilibrium on offset-stripped values, optional Guo
+// body force, and the Smagorinsky closure.
+// ---------------------------------------------------------------------------
+template <int Q, typename T, int CLOSURE>
+__device__ __forceinline__ void collide_node(T (&h)[Q], bool forced, const KParams<T> &p)
+{
+    if (CLOSURE == LBM_CLOSURE_STREAM_ONLY) return;
+    // Moments of the pulled set: rho = 1 + sum h, j = sum c h.
+    T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        drho += h[i];
+        if (cvel(i, 0)) jx += cvel(i, 0) > 0 ? h[i] : -h[i];
+        if (cvel(i, 1)) jy += cvel(i, 1) > 0 ? h[i] : -h[i];
+        if (cvel(i, 2)) jz += cvel(i, 2) > 0 ? h[i] : -h[i];
+    }
+    const T rho = T(1) + drho;
+    T Gx = T(0), Gy = T(0), Gz = T(0);
+    if (forced) {
+        Gx = rho * p.force[0];
+        Gy = rho * p.force[1];
+        Gz = rho * p.force[2];
+        jx += T(0.5) * Gx;
+        jy += T(0.5) * Gy;
+        jz += T(0.5) * Gz;
+    }
+    const T inv = T(1) / rho;
+    const T ux = jx * inv, uy = jy * inv, uz = jz * inv;
+    const T usq15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
+
+    T omega = p.omega;
+    if (CLOSURE == LBM_CLOSURE_SMAGORINSKY) {
+        // Pi^neq_ab = sum c_a c_b (f - f_eq) = sum c_a c_b h - rho u_a u_b
+        //             - (drho / 3) delta_ab   (closed-form equilibrium moments).
+        T sxx = T(0), syy = T(0), szz = T(0), sxy = T(0), sxz = T(0), syz = T(0);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
+            if (cx) sxx += h[i];
+            if (cy) syy += h[i];
+            if (cz) szz += h[i];
+            if (cx * cy) sxy += cx * cy > 0 ? h[i] : -h[i];
+            if (cx * cz) sxz += cx * cz > 0 ? h[i] : -h[i];
+            if (cy * cz) syz += cy * cz > 0 ? h[i] : -h[i];
+        }
+        const T d3 = drho * (T(1) / T(3));
+        const T pxx = sxx - rho * ux * ux - d3, pyy = syy - rho * uy * uy - d3, pzz = szz - rho * uz * uz - d3;
+        const T pxy = sxy - rho * ux * uy, pxz = sxz - rho * ux * uz, pyz = syz - rho * uy * uz;
+        const T pp = pxx * pxx + pyy * pyy + pzz * pzz + T(2) * (pxy * pxy + pxz * pxz + pyz * pyz);
+        const T te = T(0.5) * (p.tau + sqrt(p.tau * p.tau + p.smag18 * sqrt(T(2) * pp) * inv));
+        omega = T(1) / te;
+    }
+
+    const T cf = T(1) - T(0.5) * omega;
+    const T uG = ux * Gx + uy * Gy + uz * Gz;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
+        const T cu = T(cx) * ux + T(cy) * uy + T(cz) * uz;
+        const T w = wgt<T>(Q, i);
+        // h_eq = f_eq - w = w (drho + rho (3 cu + 4.5 cu^2 - 1.5 u^2))
+        const T heq = w * (drho + rho * (cu * (T(3) + T(4.5) * cu) - usq15));
+        T hn = h[i] + omega * (heq - h[i]);
+        if (forced) {
+            // Guo: F_i = w [3 (c - u) + 9 (c.u) c] . G
+            const T cG = T(cx) * Gx + T(cy) * Gy + T(cz) * Gz;
+            hn += cf * w * (T(3) * (cG - uG) + T(9) * cu * cG);
+        }
+        h[i] = hn;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused collide-and-stream (pull, two populations), one node per thread.
 //   GENERAL: tags are read (bounce-back, Ladd walls, forced nodes); without
 //            it every node is a plain fluid node and no tag byte is touched.
 //   CLOSURE: LBM_CLOSURE_BGK, _SMAGORINSKY or _STREAM_ONLY.
@@ -85,102 +193,164 @@ __global__ void __launch_bounds__(kStepThreads)
     T h[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) h[i] = St::ld(A + (long long)i * g.sN + nb.src(i));
+    if (GENERAL && (t & kNearWall)) apply_walls<Q, S>(h, A, tags, g, nb, p);
 
-    if (GENERAL && (t & kNearWall)) {
-        // Halfway bounce-back from a SOLID source; Ladd's moving-wall term
-        // 6 w_i rho_wall (c_i . u_wall) from a WALL source.
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const unsigned ts = tags[nb.src(i)] & kTagMask;
-            if (is_wall_tag(ts)) {
-                T v = St::ld(A + (long long)opp(i) * g.sN + nb.self);
-                if (ts >= LBM_TAG_WALL0) {
-                    // select the wall's velocity without indexing the parameter
-                    // block dynamically (which would copy it to local memory)
-                    T ux = T(0), uy = T(0), uz = T(0);
-#pragma unroll
-                    for (int k = 0; k < LBM_NWALLS; ++k)
-                        if (ts == (unsigned)(LBM_TAG_WALL0 + k)) {
-                            ux = p.wall6[k][0];
-                            uy = p.wall6[k][1];
-                            uz = p.wall6[k][2];
-                        }
-                    v += wgt<T>(Q, i) * (T(cvel(i, 0)) * ux + T(cvel(i, 1)) * uy + T(cvel(i, 2)) * uz);
-                }
-                h[i] = v;
-            }
-        }
-    }
-
-    if (CLOSURE != LBM_CLOSURE_STREAM_ONLY) {
-        // Moments of the pulled set: rho = 1 + sum h, j = sum c h.
-        T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            drho += h[i];
-            if (cvel(i, 0)) jx += cvel(i, 0) > 0 ? h[i] : -h[i];
-            if (cvel(i, 1)) jy += cvel(i, 1) > 0 ? h[i] : -h[i];
-            if (cvel(i, 2)) jz += cvel(i, 2) > 0 ? h[i] : -h[i];
-        }
-        const T rho = T(1) + drho;
-        T Gx = T(0), Gy = T(0), Gz = T(0);
-        const bool forced = GENERAL && (t & kTagMask) == LBM_TAG_FORCED;
-        if (forced) {
-            Gx = rho * p.force[0];
-            Gy = rho * p.force[1];
-            Gz = rho * p.force[2];
-            jx += T(0.5) * Gx;
-            jy += T(0.5) * Gy;
-            jz += T(0.5) * Gz;
-        }
-        const T inv = T(1) / rho;
-        const T ux = jx * inv, uy = jy * inv, uz = jz * inv;
-        const T usq15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
-
-        T omega = p.omega;
-        if (CLOSURE == LBM_CLOSURE_SMAGORINSKY) {
-            // Pi^neq_ab = sum c_a c_b (f - f_eq) = sum c_a c_b h - rho u_a u_b
-            //             - (drho / 3) delta_ab   (closed-form equilibrium moments).
-            T sxx = T(0), syy = T(0), szz = T(0), sxy = T(0), sxz = T(0), syz = T(0);
-#pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
-                if (cx) sxx += h[i];
-                if (cy) syy += h[i];
-                if (cz) szz += h[i];
-                if (cx * cy) sxy += cx * cy > 0 ? h[i] : -h[i];
-                if (cx * cz) sxz += cx * cz > 0 ? h[i] : -h[i];
-                if (cy * cz) syz += cy * cz > 0 ? h[i] : -h[i];
-            }
-            const T d3 = drho * (T(1) / T(3));
-            const T pxx = sxx - rho * ux * ux - d3, pyy = syy - rho * uy * uy - d3, pzz = szz - rho * uz * uz - d3;
-            const T pxy = sxy - rho * ux * uy, pxz = sxz - rho * ux * uz, pyz = syz - rho * uy * uz;
-            const T pp = pxx * pxx + pyy * pyy + pzz * pzz + T(2) * (pxy * pxy + pxz * pxz + pyz * pyz);
-            const T te = T(0.5) * (p.tau + sqrt(p.tau * p.tau + p.smag18 * sqrt(T(2) * pp) * inv));
-            omega = T(1) / te;
-        }
-
-        const T cf = T(1) - T(0.5) * omega;
-        const T uG = ux * Gx + uy * Gy + uz * Gz;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
-            const T cu = T(cx) * ux + T(cy) * uy + T(cz) * uz;
-            const T w = wgt<T>(Q, i);
-            // h_eq = f_eq - w = w (drho + rho (3 cu + 4.5 cu^2 - 1.5 u^2))
-            const T heq = w * (drho + rho * (cu * (T(3) + T(4.5) * cu) - usq15));
-            T hn = h[i] + omega * (heq - h[i]);
-            if (forced) {
-                // Guo: F_i = w [3 (c - u) + 9 (c.u) c] . G
-                const T cG = T(cx) * Gx + T(cy) * Gy + T(cz) * Gz;
-                hn += cf * w * (T(3) * (cG - uG) + T(9) * cu * cG);
-            }
-            h[i] = hn;
-        }
-    }
+    collide_node<Q, T, CLOSURE>(h, GENERAL && (t & kTagMask) == LBM_TAG_FORCED, p);
 
 #pragma unroll
     for (int i = 0; i < Q; ++i) St::st(B + (long long)i * g.sN + nb.self, h[i]);
+}
+
+// ---------------------------------------------------------------------------
+// The same step with two x-adjacent nodes (x0 = 2t, x0 + 1) per thread, for
+// 16-bit storage, where one node per thread is instruction-bound: populations
+// move as aligned 32-bit pairs with packed conversions, and the +-1 x shift of
+// the pull comes from the neighbouring lane's pair by a warp shuffle.  Only
+// the first and last lane of a warp, and the nodes at the periodic x seam,
+// load their shifted value directly.  Requires blockDim.x to be a multiple of
+// 32 so that a warp covers 64 consecutive nodes of one row; every lane takes
+// part in the shuffles, lanes past the row end only clamp their addresses.
+// ---------------------------------------------------------------------------
+template <typename S> struct Pair;
+template <> struct Pair<__half> {
+    static __device__ __forceinline__ float2 ld(const __half *p)
+    {
+        const unsigned v = __ldg(reinterpret_cast<const unsigned *>(p));
+        return __half22float2(*reinterpret_cast<const __half2 *>(&v));
+    }
+    static __device__ __forceinline__ void st(__half *p, float a, float b)
+    {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
+    }
+};
+template <> struct Pair<__nv_bfloat16> {
+    static __device__ __forceinline__ float2 ld(const __nv_bfloat16 *p)
+    {
+        const unsigned v = __ldg(reinterpret_cast<const unsigned *>(p));
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v));
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float a, float b)
+    {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+    }
+};
+template <> struct Pair<float> {
+    static __device__ __forceinline__ float2 ld(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+    static __device__ __forceinline__ void st(float *p, float a, float b)
+    {
+        *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+    }
+};
+
+template <int Q, typename S, bool GENERAL, int CLOSURE>
+__global__ void __launch_bounds__(kStepThreads)
+    k_collide_stream_x2(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ tags, Grid g,
+                        KParams<float> p)
+{
+    using St = Store<S>;
+    const int pair = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (y >= g.ny) return;  // uniform over the warp: a warp lies in one row
+    const unsigned lane = threadIdx.x & 31u;
+    const int x0 = 2 * pair;
+    const bool va = x0 < g.nx, vb = x0 + 1 < g.nx;
+    const int xc = x0 < g.px ? x0 : g.px - 2;  // in-row address for lanes past the end
+
+    int row[3][3];
+    {
+        const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+        const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+        const int ys[3] = {ym, y, yp};
+        const int zs[3] = {zm, z, zp};
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) row[a][b] = (zs[b] * g.ny + ys[a]) * g.px;
+    }
+    const int self = row[1][1] + xc;
+
+    unsigned ta = 0, tb = 0;
+    bool act_a = va, act_b = vb;
+    if (GENERAL) {
+        const unsigned tt = __ldg(reinterpret_cast<const unsigned short *>(tags + self));
+        ta = tt & 0xffu;
+        tb = tt >> 8;
+        act_a = va && !is_wall_tag(ta & kTagMask);
+        act_b = vb && !is_wall_tag(tb & kTagMask);
+    }
+
+    float2 h[Q];  // .x: node x0, .y: node x0 + 1
+    const bool edge_lo = lane == 0 || x0 == 0;               // source x0 - 1 not in lane - 1
+    const bool edge_hi = lane == 31 || x0 + 2 >= g.nx;       // source x0 + 2 not in lane + 1
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const S *Ai = A + (long long)i * g.sN + row[1 - cvel(i, 1)][1 - cvel(i, 2)];
+        const float2 P = Pair<S>::ld(Ai + xc);
+        if (cvel(i, 0) == 0) {
+            h[i] = P;
+        } else if (cvel(i, 0) > 0) {  // pull from x - 1
+            float up = __shfl_up_sync(0xffffffffu, P.y, 1);
+            if (edge_lo && va) up = St::ld(Ai + (x0 == 0 ? g.nx - 1 : x0 - 1));
+            h[i] = make_float2(up, P.x);
+        } else {  // pull from x + 1
+            float dn = __shfl_down_sync(0xffffffffu, P.x, 1);
+            if (edge_hi && vb) dn = St::ld(Ai + (x0 + 2 == g.nx ? 0 : x0 + 2));
+            h[i] = make_float2(vb ? P.y : St::ld(Ai), dn);  // odd nx: the last node wraps to x = 0
+        }
+    }
+
+    bool fa = false, fb = false;
+    if (GENERAL) {
+        if (act_a && (ta & kNearWall)) {
+            Nbr nb;
+            nb.init(g, x0, y, z);
+            float t[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) t[i] = h[i].x;
+            apply_walls<Q, S>(t, A, tags, g, nb, p);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) h[i].x = t[i];
+        }
+        if (act_b && (tb & kNearWall)) {
+            Nbr nb;
+            nb.init(g, x0 + 1, y, z);
+            float t[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) t[i] = h[i].y;
+            apply_walls<Q, S>(t, A, tags, g, nb, p);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) h[i].y = t[i];
+        }
+        fa = (ta & kTagMask) == LBM_TAG_FORCED;
+        fb = (tb & kTagMask) == LBM_TAG_FORCED;
+    }
+    {
+        // The two nodes collide one after the other in scalar FP32: a packed
+        // FP32x2 collision issues fewer instructions but needs about 84
+        // registers, and the occupancy it loses costs more than it saves.
+        float ta_[Q], tb_[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            ta_[i] = h[i].x;
+            tb_[i] = h[i].y;
+        }
+        collide_node<Q, float, CLOSURE>(ta_, fa, p);
+        collide_node<Q, float, CLOSURE>(tb_, fb, p);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) h[i] = make_float2(ta_[i], tb_[i]);
+    }
+
+    if (act_a && act_b) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Pair<S>::st(B + (long long)i * g.sN + self, h[i].x, h[i].y);
+    } else if (act_a || act_b) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (act_a) St::st(B + (long long)i * g.sN + self, h[i].x);
+            if (act_b) St::st(B + (long long)i * g.sN + self + 1, h[i].y);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -428,11 +598,46 @@ inline void node_launch_shape(const Grid &g, dim3 &grid, dim3 &block)
 // ---------------------------------------------------------------------------
 // Launchers, defined once per storage type S by LBM_DEFINE_LAUNCHERS(S).
 // ---------------------------------------------------------------------------
+// Two nodes per thread for 16-bit storage on rows of at least 64 nodes.
+template <typename S> constexpr bool use_pairs() { return sizeof(S) == 2; }
+
+inline void pair_launch_shape(const Grid &g, dim3 &grid, dim3 &block)
+{
+    const int pairs = g.px / 2;                  // px is a multiple of 32
+    const int bx = pairs >= 64 ? 64 : 32;        // whole warps along x
+    const int by = kStepThreads / bx;
+    block = dim3(bx, by, 1);
+    grid = dim3((pairs + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
+}
+
+template <int Q, typename S, bool GEN>
+cudaError_t step_closure_x2(const Launch &L, const KParams<float> &kp)
+{
+    dim3 grid, block;
+    pair_launch_shape(L.g, grid, block);
+    const S *A = (const S *)L.A;
+    S *B = (S *)L.B;
+    switch (L.closure) {
+    case LBM_CLOSURE_BGK: k_collide_stream_x2<Q, S, GEN, LBM_CLOSURE_BGK><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp); break;
+    case LBM_CLOSURE_SMAGORINSKY:
+        k_collide_stream_x2<Q, S, GEN, LBM_CLOSURE_SMAGORINSKY><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp);
+        break;
+    case LBM_CLOSURE_STREAM_ONLY:
+        k_collide_stream_x2<Q, S, GEN, LBM_CLOSURE_STREAM_ONLY><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <int Q, typename S, bool GEN>
 cudaError_t step_closure(const Launch &L, const KParams<typename Store<S>::T> &kp, dim3 grid, dim3 block)
 {
     const S *A = (const S *)L.A;
     S *B = (S *)L.B;
+    if constexpr (use_pairs<S>()) {
+        if (L.g.px >= 64) return step_closure_x2<Q, S, GEN>(L, kp);
+    }
     switch (L.closure) {
     case LBM_CLOSURE_BGK: k_collide_stream<Q, S, GEN, LBM_CLOSURE_BGK><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp); break;
     case LBM_CLOSURE_SMAGORINSKY:

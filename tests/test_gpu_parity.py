@@ -241,10 +241,16 @@ def ulp(h, kind):
     return np.exp2(e - mant)
 
 
+# 16-bit storage runs two nodes per thread when the padded row has >= 64
+# nodes: shapes cover odd nx (last node wraps), one and several warps per row,
+# a partial last block, and the one-node-per-thread kernel (px = 32).
+HALF_SHAPES = [(10, 12, 50), (5, 7, 45), (4, 6, 150), (3, 5, 64), (6, 5, 31)]
+
+
+@pytest.mark.parametrize("shape", HALF_SHAPES)
 @pytest.mark.parametrize("kind", ["f16", "bf16"])
 @pytest.mark.parametrize("Q", [19, 27])
-def test_half_storage_one_step(kind, Q):
-    shape = (10, 12, 50)
+def test_half_storage_one_step(kind, Q, shape):
     _, w, _ = oracle.lattice(Q)
     tags = inp.random_tags(shape, seed=6, p_solid=0.1, p_forced=0.3, p_wall=0.05, n_walls=2)
     walls = [(0.02, 0.0, 0.0), (0.0, 0.01, -0.01)]
@@ -263,6 +269,30 @@ def test_half_storage_one_step(kind, Q):
     diff = np.abs(hg - hr)
     excess = diff - (ulp(hr, kind) * 1.0000001 + 1e-8)
     assert np.all(excess <= 0), f"worst excess {excess.max():.3e} at |h| = {abs(hr.ravel()[excess.argmax()]):.3e}"
+    assert np.mean(diff == 0) >= 0.99
+    lat.close()
+
+
+@pytest.mark.parametrize("shape", HALF_SHAPES)
+@pytest.mark.parametrize("kind", ["f16", "bf16"])
+@pytest.mark.parametrize("Q,closure", [(19, lbm.CLOSURE_BGK), (27, lbm.CLOSURE_BGK), (19, lbm.CLOSURE_SMAGORINSKY)])
+def test_half_storage_one_step_periodic(kind, Q, closure, shape):
+    """All-fluid lattice: the kernel variant that reads no tags."""
+    _, w, _ = oracle.lattice(Q)
+    params = dict(tau=0.55, closure=closure, cs_smag=0.15)
+    rho, u = inp.random_velocity_field(shape, seed=13, amplitude=0.08)
+    prob = oracle_problem(shape, Q, None, **params)
+    f0 = oracle.round_storage(prob.init_equilibrium(rho, u), DT[kind])
+    lat = make(shape, Q, kind, None, **params)
+    lat.set_populations(f0)
+    lat.step(1)
+    f = lat.get_populations()
+    g = oracle.round_storage(prob.step(f0, 1), DT[kind])
+    wv = w.reshape(-1, 1, 1, 1)
+    hg, hr = f - wv, g - wv
+    diff = np.abs(hg - hr)
+    excess = diff - (ulp(hr, kind) * 1.0000001 + 1e-8)
+    assert np.all(excess <= 0), f"worst excess {excess.max():.3e}"
     assert np.mean(diff == 0) >= 0.99
     lat.close()
 
