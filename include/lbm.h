@@ -209,6 +209,65 @@ lbm_status lbm_geometry_spheres(lbm_ctx *ctx, const int32_t *centres, const doub
  * storage, FP32 otherwise, accumulated in FP64.  Synchronizes. */
 lbm_status lbm_enstrophy(lbm_ctx *ctx, double *out);
 
+/* ---------------------------------------------------------------------------
+ * Learned relaxation-time closure (no counterpart in the paper; an addition
+ * of this library).  Per fluid node, with Pi^neq the non-equilibrium stress
+ * sum_i c_i c_i (f_i - f_eq_i) of the pulled populations:
+ *   x   = (Pi_xx, Pi_yy, Pi_zz, Pi_xy, Pi_xz, Pi_yz, rho), normalised as
+ *         (x - mean) / std,
+ *   y   = w3 . SiLU(W2 SiLU(W1 x_n + b1) + b2) + b3,
+ *   tau_eff = tau + out_scale * softplus(y).
+ * Normalised inputs, W1, the first activations and W2 are rounded to BF16
+ * (nearest even) and multiplied on the tensor cores with FP32 accumulation;
+ * biases, the second activations and the last layer are FP32.
+ * params[LBM_MLP_NPARAM] = W1[32][7], b1[32], W2[32][32], b2[32], w3[32], b3;
+ * norm[LBM_MLP_NNORM]    = mean[7], std[7] (> 0), out_scale (>= 0), unused.
+ * ------------------------------------------------------------------------- */
+#define LBM_MLP_NPARAM 1345
+#define LBM_MLP_NNORM 16
+
+/* Installs the closure weights used by LBM_CLOSURE_MLP (copied; host or
+ * device pointers).  Synchronizes.  Errors: ARG (non-finite value, std <= 0,
+ * out_scale < 0), OOM, CUDA.  lbm_step with LBM_CLOSURE_MLP and no weights
+ * returns LBM_ERR_STATE. */
+lbm_status lbm_set_closure_weights(lbm_ctx *ctx, const float *params, const float *norm, int on_device);
+
+/* dtau[n] for features x[n][7] with the collide kernel's tensor-core tile.
+ * All pointers are device memory; asynchronous on stream.  Errors: ARG,
+ * CUDA (launch). */
+lbm_status lbm_mlp_forward(const float *params, const float *norm, const float *x, int n, float *dtau, void *stream);
+
+/* Bytes of device workspace lbm_mlp_loss_grad needs for n samples. */
+size_t lbm_mlp_workspace_bytes(int n);
+
+/* Mean squared error L = (1/n) sum (dtau - target)^2 of the closure on n
+ * samples and its gradient grad[LBM_MLP_NPARAM] with respect to params,
+ * through the same BF16 roundings as the forward pass (treated as identities
+ * for the gradient).  Deterministic: per-block sums over fixed sample sets,
+ * added in block order.  All pointers are device memory; loss may be NULL.
+ * Asynchronous.  Errors: ARG (n < 1, workspace too small), CUDA. */
+lbm_status lbm_mlp_loss_grad(const float *params, const float *norm, const float *x, const float *target, int n,
+                             float *grad, float *loss, void *workspace, size_t workspace_bytes, void *stream);
+
+/* One Adam step (Kingma & Ba) on n_params FP32 master weights, step number
+ * t >= 1: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * params -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).  Device
+ * pointers; asynchronous.  Errors: ARG, CUDA. */
+lbm_status lbm_mlp_adam(float *params, float *m, float *v, const float *grad, int n_params, int t, float lr,
+                        float beta1, float beta2, float eps, void *stream);
+
+/* Training samples from a fine field (rho[N], u[3][N], device FP64, unpadded
+ * x-fastest, periodic): for every coarse cell of a box filter of width
+ * factor, the features x[Nc][7] = (-(2/3) rho_bar tau0 S_bar, rho_bar)
+ * (Chapman-Enskog estimate of Pi^neq from the filtered strain S_bar, which
+ * uses second-order central differences of the filtered velocity on the
+ * coarse grid) and the target dtau* = 3 max(0, -tau_dev : S_bar /
+ * (2 S_bar : S_bar)) with the subgrid stress tau = mean(u u) - mean(u)
+ * mean(u).  Coarse cells in x-fastest order.  Asynchronous.  Errors: ARG
+ * (sizes not multiples of factor, tau0 <= 1/2), CUDA. */
+lbm_status lbm_coarse_samples(const double *rho, const double *u, int nx, int ny, int nz, int factor, double tau0,
+                              float *x, float *target, void *stream);
+
 /* Library-side sizes: bytes of one population array, x pitch in nodes,
  * number of populations.  Any pointer may be NULL. */
 lbm_status lbm_info(lbm_ctx *ctx, size_t *population_bytes, int *pitch_x, int *q);

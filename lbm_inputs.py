@@ -126,3 +126,29 @@ def random_velocity_field(shape, seed: int, amplitude: float = 0.05):
     rho = 1.0 + 0.01 * rng.uniform(-1.0, 1.0, size=shape)
     u = amplitude * rng.uniform(-1.0, 1.0, size=(3,) + tuple(shape))
     return rho, u
+
+
+def mlp_init(seed: int, n_in: int = 7, n_h: int = 32) -> np.ndarray:
+    """Initial closure weights (layout W1[32][7], b1, W2[32][32], b2, w3, b3):
+    uniform Glorot-style weights, zero biases."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    def glorot(fan_out, fan_in):
+        a = np.sqrt(6.0 / (fan_in + fan_out))
+        return rng.uniform(-a, a, size=(fan_out, fan_in))
+
+    W1 = glorot(n_h, n_in)
+    W2 = glorot(n_h, n_h)
+    w3 = glorot(1, n_h)[0]
+    return np.concatenate([W1.ravel(), np.zeros(n_h), W2.ravel(), np.zeros(n_h), w3, [0.0]])
+
+
+def mlp_samples(n: int, seed: int, scale: float = 1e-3):
+    """Random closure features (n, 7): stress-like components ~ N(0, scale),
+    density ~ 1 + N(0, 0.01); and positive targets ~ scale * U(0, 1)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    X = np.empty((n, 7))
+    X[:, :6] = rng.normal(0.0, scale, size=(n, 6))
+    X[:, 6] = 1.0 + rng.normal(0.0, 0.01, size=n)
+    y = scale * rng.uniform(0.0, 1.0, size=n)
+    return X, y

@@ -27,6 +27,7 @@ struct lbm_ctx {
     double *partials = nullptr; // kRedBlocks x kRedSlots reduction scratch
     double *red_out = nullptr;  // kRedSlots final sums
     unsigned long long *census_dev = nullptr;  // LBM_NTAGS + 1 counters
+    float *mlp_params = nullptr;  // closure weights (LBM_MLP_NPARAM) + normalisation (LBM_MLP_NNORM)
     cudaStream_t stream = nullptr;
     lbm_allocator alloc{};
     bool has_alloc = false;
@@ -105,7 +106,8 @@ Launch make_launch(lbm_ctx *ctx)
     L.tags = ctx->tags;
     L.general = ctx->general;
     L.closure = ctx->params.closure;
-    L.mlp = nullptr;
+    L.mlp_params = ctx->mlp_params;
+    L.mlp_norm = ctx->mlp_params ? ctx->mlp_params + LBM_MLP_NPARAM : nullptr;
     L.stream = ctx->stream;
     return L;
 }
@@ -268,6 +270,7 @@ lbm_status lbm_destroy(lbm_ctx *ctx)
     dev_free(ctx, ctx->partials, sizeof(double) * kRedBlocks * kRedSlots);
     dev_free(ctx, ctx->red_out, sizeof(double) * kRedSlots);
     dev_free(ctx, ctx->census_dev, sizeof(unsigned long long) * (LBM_NTAGS + 1));
+    dev_free(ctx, ctx->mlp_params, sizeof(float) * (LBM_MLP_NPARAM + LBM_MLP_NNORM));
     delete ctx;
     return LBM_OK;
 }
@@ -340,7 +343,6 @@ lbm_status lbm_set_params(lbm_ctx *ctx, const lbm_params *p)
     if (!ctx || !p) return fail(ctx, LBM_ERR_ARG, "NULL argument");
     std::string why;
     if (!valid_params(p, why)) return fail(ctx, LBM_ERR_ARG, "%s", why.c_str());
-    if (p->closure == LBM_CLOSURE_MLP) return fail(ctx, LBM_ERR_ARG, "MLP closure is not available in this build");
     ctx->params = *p;
     return LBM_OK;
 }
@@ -426,6 +428,8 @@ lbm_status lbm_step(lbm_ctx *ctx, int n)
 {
     if (!ctx) return fail(ctx, LBM_ERR_ARG, "NULL context");
     if (n < 0) return fail(ctx, LBM_ERR_ARG, "n must be >= 0");
+    if (ctx->params.closure == LBM_CLOSURE_MLP && !ctx->mlp_params)
+        return fail(ctx, LBM_ERR_STATE, "MLP closure selected but no weights were set (lbm_set_closure_weights)");
     for (int k = 0; k < n; ++k) {
         Launch L = make_launch(ctx);
         CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
@@ -626,6 +630,40 @@ lbm_status lbm_enstrophy(lbm_ctx *ctx, double *out)
     if (st != LBM_OK) return st;
     *out = r[0] / (double)N;
     return LBM_OK;
+}
+
+lbm_status lbm_set_closure_weights(lbm_ctx *ctx, const float *params, const float *norm, int on_device)
+{
+    if (!ctx || !params || !norm) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    float host[LBM_MLP_NPARAM + LBM_MLP_NNORM];
+    const float *src_p = params, *src_n = norm;
+    if (on_device) {
+        CUDA_TRY(ctx, cudaMemcpyAsync(host, params, sizeof(float) * LBM_MLP_NPARAM, cudaMemcpyDeviceToHost, ctx->stream),
+                 "weights copy");
+        CUDA_TRY(ctx, cudaMemcpyAsync(host + LBM_MLP_NPARAM, norm, sizeof(float) * LBM_MLP_NNORM, cudaMemcpyDeviceToHost,
+                                      ctx->stream),
+                 "norm copy");
+        lbm_status s = sync(ctx);
+        if (s != LBM_OK) return s;
+    } else {
+        memcpy(host, params, sizeof(float) * LBM_MLP_NPARAM);
+        memcpy(host + LBM_MLP_NPARAM, norm, sizeof(float) * LBM_MLP_NNORM);
+    }
+    src_p = host;
+    src_n = host + LBM_MLP_NPARAM;
+    for (int k = 0; k < LBM_MLP_NPARAM; ++k)
+        if (!isfinite(src_p[k])) return fail(ctx, LBM_ERR_ARG, "closure weight %d is not finite", k);
+    for (int k = 0; k < 15; ++k)
+        if (!isfinite(src_n[k])) return fail(ctx, LBM_ERR_ARG, "normalisation entry %d is not finite", k);
+    for (int k = 7; k < 14; ++k)
+        if (!(src_n[k] > 0.f)) return fail(ctx, LBM_ERR_ARG, "normalisation std %d must be > 0", k - 7);
+    if (!(src_n[14] >= 0.f)) return fail(ctx, LBM_ERR_ARG, "out_scale must be >= 0");
+    if (!ctx->mlp_params) {
+        ctx->mlp_params = (float *)dev_alloc(ctx, sizeof(float) * (LBM_MLP_NPARAM + LBM_MLP_NNORM));
+        if (!ctx->mlp_params) return fail(ctx, LBM_ERR_OOM, "closure weight allocation failed");
+    }
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->mlp_params, host, sizeof host, cudaMemcpyHostToDevice, ctx->stream), "weights upload");
+    return sync(ctx);
 }
 
 lbm_status lbm_info(lbm_ctx *ctx, size_t *population_bytes, int *pitch_x, int *q)

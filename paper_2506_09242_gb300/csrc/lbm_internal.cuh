@@ -118,7 +118,8 @@ struct Launch {
     const uint8_t *tags;      // internal padded tags
     bool general;             // tags present (not all FLUID)
     int closure;
-    const void *mlp;          // device MLP block (closure 2)
+    const float *mlp_params;  // device FP32 closure parameters (closure 2)
+    const float *mlp_norm;    // device normalisation vector (closure 2)
     cudaStream_t stream;
 };
 

@@ -8,6 +8,7 @@
 #pragma once
 
 #include "lbm_internal.cuh"
+#include "lbm_mlp.cuh"
 
 namespace lbm {
 
@@ -92,13 +93,19 @@ __device__ __forceinline__ void apply_walls(typename Store<S>::T (&h)[Q], const 
 // ---------------------------------------------------------------------------
 // Collision of one node's pulled set (in place), Sec. 3.1 BGK with the
 // second-order weighted equilibrium on offset-stripped values, optional Guo
-// body force, and the Smagorinsky closure.
+// body force, and the Smagorinsky closure; split into the macroscopic
+// moments, the non-equilibrium stress and the relaxation so that the learned
+// closure can run between them.
 // ---------------------------------------------------------------------------
-template <int Q, typename T, int CLOSURE>
-__device__ __forceinline__ void collide_node(T (&h)[Q], bool forced, const KParams<T> &p)
+template <typename T> struct Macro {
+    T drho, rho, inv, ux, uy, uz, Gx, Gy, Gz;
+};
+
+// rho = 1 + sum h, j = sum c h (+ rho g / 2 on a forced node), u = j / rho.
+template <int Q, typename T>
+__device__ __forceinline__ Macro<T> node_macros(const T (&h)[Q], bool forced, const KParams<T> &p)
 {
-    if (CLOSURE == LBM_CLOSURE_STREAM_ONLY) return;
-    // Moments of the pulled set: rho = 1 + sum h, j = sum c h.
+    Macro<T> m;
     T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -107,60 +114,88 @@ __device__ __forceinline__ void collide_node(T (&h)[Q], bool forced, const KPara
         if (cvel(i, 1)) jy += cvel(i, 1) > 0 ? h[i] : -h[i];
         if (cvel(i, 2)) jz += cvel(i, 2) > 0 ? h[i] : -h[i];
     }
-    const T rho = T(1) + drho;
-    T Gx = T(0), Gy = T(0), Gz = T(0);
+    m.drho = drho;
+    m.rho = T(1) + drho;
+    m.Gx = m.Gy = m.Gz = T(0);
     if (forced) {
-        Gx = rho * p.force[0];
-        Gy = rho * p.force[1];
-        Gz = rho * p.force[2];
-        jx += T(0.5) * Gx;
-        jy += T(0.5) * Gy;
-        jz += T(0.5) * Gz;
+        m.Gx = m.rho * p.force[0];
+        m.Gy = m.rho * p.force[1];
+        m.Gz = m.rho * p.force[2];
+        jx += T(0.5) * m.Gx;
+        jy += T(0.5) * m.Gy;
+        jz += T(0.5) * m.Gz;
     }
-    const T inv = T(1) / rho;
-    const T ux = jx * inv, uy = jy * inv, uz = jz * inv;
-    const T usq15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
+    m.inv = T(1) / m.rho;
+    m.ux = jx * m.inv;
+    m.uy = jy * m.inv;
+    m.uz = jz * m.inv;
+    return m;
+}
 
-    T omega = p.omega;
-    if (CLOSURE == LBM_CLOSURE_SMAGORINSKY) {
-        // Pi^neq_ab = sum c_a c_b (f - f_eq) = sum c_a c_b h - rho u_a u_b
-        //             - (drho / 3) delta_ab   (closed-form equilibrium moments).
-        T sxx = T(0), syy = T(0), szz = T(0), sxy = T(0), sxz = T(0), syz = T(0);
+// Pi^neq_ab = sum c_a c_b (f - f_eq) = sum c_a c_b h - rho u_a u_b
+//             - (drho / 3) delta_ab   (closed-form equilibrium moments);
+// order xx, yy, zz, xy, xz, yz.
+template <int Q, typename T>
+__device__ __forceinline__ void pi_neq(const T (&h)[Q], const Macro<T> &m, T (&pi)[6])
+{
+    T sxx = T(0), syy = T(0), szz = T(0), sxy = T(0), sxz = T(0), syz = T(0);
 #pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
-            if (cx) sxx += h[i];
-            if (cy) syy += h[i];
-            if (cz) szz += h[i];
-            if (cx * cy) sxy += cx * cy > 0 ? h[i] : -h[i];
-            if (cx * cz) sxz += cx * cz > 0 ? h[i] : -h[i];
-            if (cy * cz) syz += cy * cz > 0 ? h[i] : -h[i];
-        }
-        const T d3 = drho * (T(1) / T(3));
-        const T pxx = sxx - rho * ux * ux - d3, pyy = syy - rho * uy * uy - d3, pzz = szz - rho * uz * uz - d3;
-        const T pxy = sxy - rho * ux * uy, pxz = sxz - rho * ux * uz, pyz = syz - rho * uy * uz;
-        const T pp = pxx * pxx + pyy * pyy + pzz * pzz + T(2) * (pxy * pxy + pxz * pxz + pyz * pyz);
-        const T te = T(0.5) * (p.tau + sqrt(p.tau * p.tau + p.smag18 * sqrt(T(2) * pp) * inv));
-        omega = T(1) / te;
+    for (int i = 1; i < Q; ++i) {
+        const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
+        if (cx) sxx += h[i];
+        if (cy) syy += h[i];
+        if (cz) szz += h[i];
+        if (cx * cy) sxy += cx * cy > 0 ? h[i] : -h[i];
+        if (cx * cz) sxz += cx * cz > 0 ? h[i] : -h[i];
+        if (cy * cz) syz += cy * cz > 0 ? h[i] : -h[i];
     }
+    const T d3 = m.drho * (T(1) / T(3));
+    pi[0] = sxx - m.rho * m.ux * m.ux - d3;
+    pi[1] = syy - m.rho * m.uy * m.uy - d3;
+    pi[2] = szz - m.rho * m.uz * m.uz - d3;
+    pi[3] = sxy - m.rho * m.ux * m.uy;
+    pi[4] = sxz - m.rho * m.ux * m.uz;
+    pi[5] = syz - m.rho * m.uy * m.uz;
+}
 
+// h_i <- h_i + omega (h_eq_i - h_i) + (1 - omega / 2) F_i.
+template <int Q, typename T>
+__device__ __forceinline__ void relax(T (&h)[Q], const Macro<T> &m, T omega, bool forced)
+{
+    const T usq15 = T(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
     const T cf = T(1) - T(0.5) * omega;
-    const T uG = ux * Gx + uy * Gy + uz * Gz;
+    const T uG = m.ux * m.Gx + m.uy * m.Gy + m.uz * m.Gz;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
-        const T cu = T(cx) * ux + T(cy) * uy + T(cz) * uz;
+        const T cu = T(cx) * m.ux + T(cy) * m.uy + T(cz) * m.uz;
         const T w = wgt<T>(Q, i);
         // h_eq = f_eq - w = w (drho + rho (3 cu + 4.5 cu^2 - 1.5 u^2))
-        const T heq = w * (drho + rho * (cu * (T(3) + T(4.5) * cu) - usq15));
+        const T heq = w * (m.drho + m.rho * (cu * (T(3) + T(4.5) * cu) - usq15));
         T hn = h[i] + omega * (heq - h[i]);
         if (forced) {
             // Guo: F_i = w [3 (c - u) + 9 (c.u) c] . G
-            const T cG = T(cx) * Gx + T(cy) * Gy + T(cz) * Gz;
+            const T cG = T(cx) * m.Gx + T(cy) * m.Gy + T(cz) * m.Gz;
             hn += cf * w * (T(3) * (cG - uG) + T(9) * cu * cG);
         }
         h[i] = hn;
     }
+}
+
+template <int Q, typename T, int CLOSURE>
+__device__ __forceinline__ void collide_node(T (&h)[Q], bool forced, const KParams<T> &p)
+{
+    if (CLOSURE == LBM_CLOSURE_STREAM_ONLY) return;
+    const Macro<T> m = node_macros<Q, T>(h, forced, p);
+    T omega = p.omega;
+    if (CLOSURE == LBM_CLOSURE_SMAGORINSKY) {
+        T pi[6];
+        pi_neq<Q, T>(h, m, pi);
+        const T pp = pi[0] * pi[0] + pi[1] * pi[1] + pi[2] * pi[2] + T(2) * (pi[3] * pi[3] + pi[4] * pi[4] + pi[5] * pi[5]);
+        const T te = T(0.5) * (p.tau + sqrt(p.tau * p.tau + p.smag18 * sqrt(T(2) * pp) * m.inv));
+        omega = T(1) / te;
+    }
+    relax<Q, T>(h, m, omega, forced);
 }
 
 // ---------------------------------------------------------------------------
@@ -199,6 +234,59 @@ __global__ void __launch_bounds__(kStepThreads)
 
 #pragma unroll
     for (int i = 0; i < Q; ++i) St::st(B + (long long)i * g.sN + nb.self, h[i]);
+}
+
+// ---------------------------------------------------------------------------
+// The step with the learned closure: tau_eff = tau + dtau(Pi^neq, rho) per
+// node, the network evaluated by each warp on its 32 nodes as a BF16
+// tensor-core tile (mlp_warp_dtau).  Every lane of a warp takes part in the
+// network, so lanes past the row end and solid nodes only skip their loads
+// and stores.  Requires blockDim.x to be a multiple of 32.
+// ---------------------------------------------------------------------------
+template <int Q, typename S, bool GENERAL>
+__global__ void __launch_bounds__(kStepThreads)
+    k_collide_stream_mlp(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ tags, Grid g,
+                         KParams<typename Store<S>::T> p, const float *__restrict__ mlp_params,
+                         const float *__restrict__ mlp_norm)
+{
+    using T = typename Store<S>::T;
+    using St = Store<S>;
+    __shared__ MlpSmem W;
+    __shared__ uint32_t stage[kStepThreads / 32][32 * 8];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    load_mlp_smem(mlp_params, mlp_norm, W, tid, blockDim.x * blockDim.y);
+    __syncthreads();
+
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (y >= g.ny) return;  // uniform over the warp: a warp lies in one row
+    const bool inx = x < g.nx;
+    Nbr nb;
+    nb.init(g, inx ? x : 0, y, z);
+    unsigned t = 0;
+    bool active = inx;
+    if (GENERAL && inx) {
+        t = tags[nb.self];
+        active = !is_wall_tag(t & kTagMask);
+    }
+    T h[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) h[i] = active ? St::ld(A + (long long)i * g.sN + nb.src(i)) : T(0);
+    if (GENERAL && active && (t & kNearWall)) apply_walls<Q, S>(h, A, tags, g, nb, p);
+
+    const bool forced = GENERAL && (t & kTagMask) == LBM_TAG_FORCED;
+    const Macro<T> m = node_macros<Q, T>(h, forced, p);
+    T pi[6];
+    pi_neq<Q, T>(h, m, pi);
+    const float xf[kMlpIn] = {(float)pi[0], (float)pi[1], (float)pi[2], (float)pi[3],
+                              (float)pi[4], (float)pi[5], (float)m.rho};
+    const float dtau = mlp_warp_dtau(W, stage[tid >> 5], xf, (unsigned)tid & 31u);
+    relax<Q, T>(h, m, T(1) / (p.tau + T(dtau)), forced);
+    if (active) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) St::st(B + (long long)i * g.sN + nb.self, h[i]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -635,6 +723,11 @@ cudaError_t step_closure(const Launch &L, const KParams<typename Store<S>::T> &k
 {
     const S *A = (const S *)L.A;
     S *B = (S *)L.B;
+    if (L.closure == LBM_CLOSURE_MLP) {
+        if (!L.mlp_params || !L.mlp_norm) return cudaErrorInvalidValue;
+        k_collide_stream_mlp<Q, S, GEN><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, L.mlp_params, L.mlp_norm);
+        return cudaGetLastError();
+    }
     if constexpr (use_pairs<S>()) {
         if (L.g.px >= 64) return step_closure_x2<Q, S, GEN>(L, kp);
     }

@@ -98,6 +98,12 @@ SIGNATURES = {
     "lbm_last_error": (ctypes.c_char_p, [_P]),
     "lbm_geometry_spheres": (_I, [_P, _P, _P, _I, _D, ctypes.c_uint8, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "lbm_enstrophy": (_I, [_P, ctypes.POINTER(_D)]),
+    "lbm_set_closure_weights": (_I, [_P, _P, _P, _I]),
+    "lbm_mlp_forward": (_I, [_P, _P, _P, _I, _P, _P]),
+    "lbm_mlp_workspace_bytes": (_SZ, [_I]),
+    "lbm_mlp_loss_grad": (_I, [_P, _P, _P, _P, _I, _P, _P, _P, _SZ, _P]),
+    "lbm_mlp_adam": (_I, [_P, _P, _P, _P, _I, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P]),
+    "lbm_coarse_samples": (_I, [_P, _P, _I, _I, _I, _I, _D, _P, _P, _P]),
     "lbm_reduce_noalloc": (_I, [_P, _I, _I, _I, _I, _I, _P, ctypes.POINTER(Params), _P, ctypes.POINTER(Reduction)]),
 }
 
@@ -346,6 +352,14 @@ class Lattice:
         self._call("lbm_enstrophy", ctypes.byref(out))
         return out.value
 
+    def set_closure_weights(self, params, norm):
+        """Installs the closure network (params[1345], norm[16]; numpy or CUDA tensors)."""
+        p, dp, _kp = _buf(params, np.float32)
+        n, dn, _kn = _buf(norm, np.float32)
+        if dp != dn:
+            raise ValueError("params and norm must both be on the host or both on the device")
+        self._call("lbm_set_closure_weights", p, n, dp)
+
     def info(self) -> dict:
         nbytes, px, q = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
         self._call("lbm_info", ctypes.byref(nbytes), ctypes.byref(px), ctypes.byref(q))
@@ -378,3 +392,66 @@ def reduce_noalloc(h, Q: int, dtype, nx: int, ny: int, nz: int, tags=None, force
         raise UnstableError(st, lib.lbm_last_error(None).decode(), out.as_dict())
     _check(st, None)
     return out.as_dict()
+
+
+# -- closure training calls (device tensors, torch's current stream) ---------
+MLP_NPARAM, MLP_NNORM = 1345, 16
+
+
+def _dev(t, dtype_name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA tensor")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise TypeError(f"expected torch.{dtype_name}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def mlp_forward(params, norm, x):
+    """dtau for features x (n, 7) on the GPU's tensor-core tile."""
+    import torch
+    n = x.shape[0]
+    out = torch.empty(n, dtype=torch.float32, device=x.device)
+    _check(load().lbm_mlp_forward(_dev(params, "float32"), _dev(norm, "float32"), _dev(x, "float32"), n,
+                                  _dev(out, "float32"), _stream()))
+    return out
+
+
+def mlp_loss_grad(params, norm, x, target, workspace=None):
+    """(loss, grad) of the mean squared dtau error over (x, target)."""
+    import torch
+    n = x.shape[0]
+    nbytes = load().lbm_mlp_workspace_bytes(n)
+    if workspace is None or workspace.numel() * 4 < nbytes:
+        workspace = torch.empty((nbytes + 3) // 4, dtype=torch.float32, device=x.device)
+    grad = torch.empty(MLP_NPARAM, dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    _check(load().lbm_mlp_loss_grad(_dev(params, "float32"), _dev(norm, "float32"), _dev(x, "float32"),
+                                    _dev(target, "float32"), n, _dev(grad, "float32"), _dev(loss, "float32"),
+                                    _dev(workspace, "float32"), workspace.numel() * 4, _stream()))
+    return loss, grad
+
+
+def mlp_adam(params, m, v, grad, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In-place Adam step on device tensors."""
+    _check(load().lbm_mlp_adam(_dev(params, "float32"), _dev(m, "float32"), _dev(v, "float32"),
+                               _dev(grad, "float32"), params.numel(), int(t), float(lr), float(beta1), float(beta2),
+                               float(eps), _stream()))
+
+
+def coarse_samples(rho, u, factor, tau0):
+    """Training features (Nc, 7) and targets (Nc,) from fine device fields
+    rho (nz, ny, nx) and u (3, nz, ny, nx), FP64."""
+    import torch
+    nz, ny, nx = rho.shape
+    nc = (nx // factor) * (ny // factor) * (nz // factor)
+    X = torch.empty((nc, 7), dtype=torch.float32, device=rho.device)
+    y = torch.empty(nc, dtype=torch.float32, device=rho.device)
+    _check(load().lbm_coarse_samples(_dev(rho, "float64"), _dev(u, "float64"), nx, ny, nz, int(factor), float(tau0),
+                                     _dev(X, "float32"), _dev(y, "float32"), _stream()))
+    return X, y

@@ -1,0 +1,156 @@
+"""GPU parity of the learned closure against the FP64 oracle (oracle/mlp.py,
+and the C oracle's closure step), both sides applying the same BF16
+roundings of inputs, first-layer weights and activations, and second-layer
+weights.
+
+Tolerances: the GPU multiplies in FP32 on the tensor cores and normalises in
+FP32, so a BF16 rounding can fall the other way than in the FP64 oracle.
+Forward: relative error <= 2e-2 everywhere and <= 2e-3 for 99% of the
+samples.  Gradient: relative L2 <= 2e-3.  Adam: relative 1e-5 (FP32).
+Training samples: relative 1e-5 (FP32 output of FP64 arithmetic).  The
+collide step with the closure: a flipped BF16 rounding changes dtau by up
+to the forward bound 2e-2 relative, hence a population by up to
+omega^2 * 2e-2 * dtau * |h - h_eq| (about 2e-5 here); 99% of the
+populations must agree to 1e-7 (FP32 arithmetic), all to 2e-5 after one
+step, and the velocity to relative L2 1e-4 after 20 steps.
+"""
+import numpy as np
+import pytest
+import torch
+
+import lbm_inputs as inp
+import oracle
+from oracle import mlp
+from paper_2506_09242_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2506_09242_gb300 import _build
+    _build.build()
+    lbm.load()
+
+
+def _params(seed=11):
+    P = inp.mlp_init(seed)
+    rng = np.random.default_rng(seed)
+    P[224:256] = rng.normal(0, 0.2, 32)      # b1
+    P[1280:1312] = rng.normal(0, 0.2, 32)    # b2
+    P[-1] = -0.5
+    return P
+
+
+def _norm(X, out_scale=1e-3):
+    std = X.std(axis=0)
+    std[std == 0] = 1.0
+    return np.concatenate([X.mean(axis=0), std, [out_scale, 0.0]])
+
+
+def _cuda32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def test_forward_matches_oracle():
+    X, _ = inp.mlp_samples(3037, seed=4)  # ragged last warp and block
+    P = _params()
+    norm = _norm(X)
+    got = lbm.mlp_forward(_cuda32(P), _cuda32(norm), _cuda32(X)).cpu().numpy().astype(np.float64)
+    # the oracle sees the FP32 values the GPU sees
+    ref, _ = mlp.forward(np.float32(P).astype(float), np.float32(norm).astype(float), np.float32(X).astype(float))
+    rel = np.abs(got - ref) / np.abs(ref)
+    assert rel.max() <= 2e-2
+    assert np.quantile(rel, 0.99) <= 2e-3
+
+
+def test_gradient_matches_oracle_and_is_deterministic():
+    X, t = inp.mlp_samples(1000, seed=5)
+    P = _params(12)
+    norm = _norm(X)
+    P32, n32, X32, t32 = (np.float32(a).astype(float) for a in (P, norm, X, t))
+    loss_ref, g_ref = mlp.loss_and_grad(P32, n32, X32, t32)
+    args = (_cuda32(P), _cuda32(norm), _cuda32(X), _cuda32(t))
+    loss1, g1 = lbm.mlp_loss_grad(*args)
+    loss2, g2 = lbm.mlp_loss_grad(*args)
+    g = g1.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g - g_ref) <= 2e-3 * np.linalg.norm(g_ref)
+    assert float(loss1.item()) == pytest.approx(loss_ref, rel=2e-3)
+    assert torch.equal(g1, g2) and torch.equal(loss1, loss2)
+
+
+def test_adam_matches_oracle():
+    rng = np.random.default_rng(3)
+    P = rng.normal(size=lbm.MLP_NPARAM)
+    m = np.zeros_like(P)
+    v = np.zeros_like(P)
+    Pd, md, vd = _cuda32(P), _cuda32(m), _cuda32(v)
+    for step in range(1, 6):
+        g = rng.normal(size=lbm.MLP_NPARAM)
+        P, m, v = mlp.adam(P, m, v, np.float32(g).astype(float), step, lr=1e-2)
+        lbm.mlp_adam(Pd, md, vd, _cuda32(g), step, 1e-2)
+    assert np.allclose(Pd.cpu().numpy(), P, rtol=1e-5, atol=1e-6)
+
+
+def test_coarse_samples_match_oracle():
+    f = 4
+    shape = (16, 12, 20)
+    rho, u = inp.random_velocity_field(shape, seed=7, amplitude=0.05)
+    # add a smooth large-scale flow so the coarse strain is not pure noise
+    _, ut = inp.tgv3d(20, 0.04)
+    u += ut[:, :16, :12, :20]
+    X, y = lbm.coarse_samples(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda(), f, 0.51)
+    Xr, yr = mlp.coarse_samples(rho, u, f, 0.51)
+    X, y = X.cpu().numpy(), y.cpu().numpy()
+    assert np.allclose(X, Xr, rtol=1e-5, atol=1e-12)
+    assert np.allclose(y, yr, rtol=1e-5, atol=1e-12)
+    assert (yr > 0).mean() > 0.1  # the fit is not trivially clipped
+
+
+@pytest.mark.parametrize("Q,kind", [(19, "f64"), (19, "f32"), (27, "f32"), (19, "bf16")])
+def test_collide_with_mlp_closure_matches_oracle(Q, kind):
+    shape = (9, 10, 40)  # ragged x: lanes past the row end still run the network
+    tags = inp.random_tags(shape, seed=8, p_solid=0.1, p_forced=0.3, p_wall=0.05, n_walls=2)
+    walls = [(0.02, 0.0, 0.0), (0.0, 0.01, 0.0)]
+    rho, u = inp.random_velocity_field(shape, seed=9, amplitude=0.05)
+    X, _ = inp.mlp_samples(512, seed=10)
+    P = _params(13)
+    norm = _norm(X, out_scale=1e-2)
+    P32, n32 = np.float32(P).astype(float), np.float32(norm).astype(float)
+    params = dict(tau=0.6, force=(1e-4, 0.0, 0.0), wall_u=walls)
+    prob = oracle.Problem(Q, shape[2], shape[1], shape[0], tags, closure=oracle.MLP, mlp_params=P32,
+                          mlp_norm=n32, mlp_bf16=True, **params)
+    dt = {"f64": oracle.F64, "f32": oracle.F32, "bf16": oracle.BF16}[kind]
+    f0 = oracle.round_storage(prob.init_equilibrium(rho, u), dt)
+    with lbm.Lattice(shape[2], shape[1], shape[0], Q, kind) as lat:
+        lat.set_tags(tags)
+        lat.set_params(closure=lbm.CLOSURE_MLP, **params)
+        lat.set_closure_weights(np.float32(P), np.float32(norm))
+        lat.set_populations(f0)
+        lat.step(1)
+        f1 = lat.get_populations()
+        lat.step(19)
+        _, ug = lat.moments()
+    g1 = prob.step(f0, 1)
+    if kind == "bf16":
+        g1 = oracle.round_storage(g1, dt)
+        c, w, _ = oracle.lattice(Q)
+        assert np.max(np.abs(f1 - g1)) <= 1e-4  # one BF16 ulp of |h| <~ 0.03
+    else:
+        d = np.abs(f1 - g1)
+        assert np.quantile(d, 0.99) <= 1e-7
+        assert d.max() <= 2e-5
+        _, ur = prob.moments(prob.step(f0, 20))
+        assert np.linalg.norm(ug - ur) <= 1e-4 * np.linalg.norm(ur)
+
+
+def test_mlp_closure_needs_weights():
+    with lbm.Lattice(32, 4, 4, 19, "f32") as lat:
+        lat.set_params(0.6, closure=lbm.CLOSURE_MLP)
+        with pytest.raises(lbm.LBMError) as e:
+            lat.step(1)
+        assert e.value.status == lbm.ERR_STATE
+        with pytest.raises(lbm.LBMError):
+            lat.set_closure_weights(np.zeros(1345, np.float32), np.zeros(16, np.float32))  # std = 0
