@@ -268,6 +268,11 @@ lbm_status lbm_mlp_adam(float *params, float *m, float *v, const float *grad, in
 lbm_status lbm_coarse_samples(const double *rho, const double *u, int nx, int ny, int nz, int factor, double tau0,
                               float *x, float *target, void *stream);
 
+/* Box filter of ncomp fields in[ncomp][N] (device FP64, unpadded, x-fastest)
+ * into out[ncomp][Nc]: the mean over each factor^3 block of nodes, coarse
+ * cells in x-fastest order.  Asynchronous.  Errors: ARG, CUDA. */
+lbm_status lbm_box_filter(const double *in, int ncomp, int nx, int ny, int nz, int factor, double *out, void *stream);
+
 /* Library-side sizes: bytes of one population array, x pitch in nodes,
  * number of populations.  Any pointer may be NULL. */
 lbm_status lbm_info(lbm_ctx *ctx, size_t *population_bytes, int *pitch_x, int *q);

@@ -1,0 +1,256 @@
+"""Learned-closure workflow on the 3D Taylor-Green vortex (orchestration only).
+
+Every numerical step runs in the CUDA library through the C ABI:
+- stepping the fine and coarse lattices;
+- moments and box filtering (`lbm_box_filter`);
+- training samples (`lbm_coarse_samples`);
+- loss gradients (`lbm_mlp_loss_grad`) and Adam (`lbm_mlp_adam`);
+- the closure inside the collide kernel;
+- the FP64 reductions.
+
+Python only sequences the calls. torch holds device buffers, draws minibatch
+indices and takes means of small filtered fields.
+
+Workflow (no counterpart in the paper; the TGV set-up is Sec. 3.1's):
+1. Fine runs at resolution n_f and Reynolds numbers Re (u0 = 0.04,
+   tau = 1/2 + 3 u0 (n_f / 2 pi) / Re). Snapshots are box-filtered by a
+   factor f into training samples for the coarse grid n_c = n_f / f. With
+   convective scaling the coarse time step is f fine steps, velocities are
+   unchanged, and time is measured in convective units t_c = n / (2 pi u0)
+   steps.
+2. The closure network is trained with Adam on minibatches of the samples.
+3. Coarse runs at n_c use plain BGK, Smagorinsky (Cs = 0.1) or the learned
+   closure. Each is judged by the relative L2 error of its dissipation rate
+   -dk/dt against that of the box-filtered fine run, where
+   k = <|u|^2 / 2> (Sec. 3.1).
+"""
+from __future__ import annotations
+
+import json
+import math
+import sys
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import lbm
+
+U0 = 0.04
+
+
+def tgv_tau(n: int, re: float, u0: float = U0) -> float:
+    return 0.5 + 3.0 * u0 * (n / (2.0 * math.pi)) / re
+
+
+def steps_per_tc(n: int, u0: float = U0) -> float:
+    return n / (2.0 * math.pi * u0)
+
+
+@dataclass
+class FineRun:
+    re: float
+    n: int
+    factor: int
+    times: np.ndarray          # convective times of the energy samples
+    k_filtered: np.ndarray     # k of the box-filtered velocity
+    X: object = None           # training features (torch, device)
+    y: object = None           # training targets (torch, device)
+    glups: float = 0.0
+    diverged_at: float | None = None
+
+
+def _tgv_fields(n):
+    import lbm_inputs as inp
+    return inp.tgv3d(n, U0)
+
+
+def fine_run(n: int, re: float, factor: int, *, t_end: float = 10.0, k_every: float = 0.1,
+             sample_every: float = 0.5, samples_per_snapshot: int = 200_000, seed: int = 0,
+             dtype: str = "f32") -> FineRun:
+    """Runs the fine TGV, records the filtered kinetic energy every k_every t_c
+    and collects training samples every sample_every t_c."""
+    import torch
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    lat = lbm.Lattice(n, n, n, lbm.D3Q19, dtype)
+    lat.set_params(tgv_tau(n, re))
+    rho, u = _tgv_fields(n)
+    lat.init_equilibrium(rho, u)
+    del rho, u
+    rho_d = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+    u_d = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
+    tau_c = tgv_tau(n // factor, re)
+    spt = steps_per_tc(n)
+    n_k = int(round(t_end / k_every))
+    every = max(1, int(round(sample_every / k_every)))
+    times, ks, Xs, ys = [], [], [], []
+    done, t_step = 0, 0.0
+    diverged = None
+    for j in range(n_k + 1):
+        target = int(round(j * k_every * spt))
+        if target > done:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lat.step(target - done)
+            torch.cuda.synchronize()
+            t_step += time.perf_counter() - t0
+            done = target
+        lat.moments(rho_d, u_d)
+        if not torch.isfinite(u_d).all():
+            diverged = j * k_every
+            break
+        ub = lbm.box_filter(u_d, factor)
+        times.append(j * k_every)
+        ks.append(0.5 * float((ub * ub).sum(dim=0).mean()))
+        if j % every == 0 and j > 0:
+            X, y = lbm.coarse_samples(rho_d, u_d, factor, tau_c)
+            idx = torch.randint(0, X.shape[0], (min(samples_per_snapshot, X.shape[0]),), generator=gen,
+                                device="cuda")
+            Xs.append(X[idx])
+            ys.append(y[idx])
+    lat.close()
+    run = FineRun(re, n, factor, np.array(times), np.array(ks), diverged_at=diverged)
+    run.glups = n ** 3 * done / max(t_step, 1e-9) / 1e9
+    if Xs:
+        run.X = torch.cat(Xs)
+        run.y = torch.cat(ys)
+    return run
+
+
+@dataclass
+class Trained:
+    params: object
+    norm: object
+    losses: list = field(default_factory=list)
+
+
+def train(X, y, *, steps: int = 2000, batch: int = 8192, lr: float = 2e-3, seed: int = 0) -> Trained:
+    """Adam on minibatches; normalisation from the sample statistics and an
+    output scale that makes y = 0 predict the mean target."""
+    import torch
+    import lbm_inputs as inp
+    mean = X.mean(dim=0)
+    std = X.std(dim=0).clamp_min(1e-12)
+    scale = float(y.mean()) / math.log(2.0) if float(y.mean()) > 0 else 1e-6
+    norm = torch.cat([mean, std, torch.tensor([scale, 0.0], device="cuda")]).float().contiguous()
+    P = torch.from_numpy(inp.mlp_init(seed).astype(np.float32)).cuda()
+    m = torch.zeros_like(P)
+    v = torch.zeros_like(P)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed + 1)
+    ws = torch.empty((lbm.load().lbm_mlp_workspace_bytes(batch) + 3) // 4, dtype=torch.float32, device="cuda")
+    losses = []
+    for t in range(1, steps + 1):
+        idx = torch.randint(0, X.shape[0], (batch,), generator=gen, device="cuda")
+        loss, grad = lbm.mlp_loss_grad(P, norm, X[idx].contiguous(), y[idx].contiguous(), ws)
+        lbm.mlp_adam(P, m, v, grad, t, lr)
+        if t % max(1, steps // 20) == 0 or t == 1:
+            losses.append((t, float(loss.item())))
+    return Trained(P, norm, losses)
+
+
+@dataclass
+class CoarseRun:
+    closure: str
+    times: np.ndarray
+    k: np.ndarray
+    glups: float
+    diverged_at: float | None
+
+
+def coarse_run(n: int, re: float, closure: str, trained: Trained | None = None, *, cs: float = 0.1,
+               t_end: float = 10.0, k_every: float = 0.1, dtype: str = "f32") -> CoarseRun:
+    import torch
+    lat = lbm.Lattice(n, n, n, lbm.D3Q19, dtype)
+    kind = {"bgk": lbm.CLOSURE_BGK, "smagorinsky": lbm.CLOSURE_SMAGORINSKY, "mlp": lbm.CLOSURE_MLP}[closure]
+    lat.set_params(tgv_tau(n, re), closure=kind, cs_smag=cs)
+    if kind == lbm.CLOSURE_MLP:
+        lat.set_closure_weights(trained.params, trained.norm)
+    rho, u = _tgv_fields(n)
+    lat.init_equilibrium(rho, u)
+    spt = steps_per_tc(n)
+    times, ks = [], []
+    done, t_step, diverged = 0, 0.0, None
+    for j in range(int(round(t_end / k_every)) + 1):
+        target = int(round(j * k_every * spt))
+        if target > done:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lat.step(target - done)
+            torch.cuda.synchronize()
+            t_step += time.perf_counter() - t0
+            done = target
+        try:
+            red = lat.reduce()
+        except lbm.UnstableError:
+            diverged = j * k_every
+            break
+        times.append(j * k_every)
+        ks.append(red["ke"] / red["n_fluid"])
+    lat.close()
+    return CoarseRun(closure, np.array(times), np.array(ks), n ** 3 * done / max(t_step, 1e-9) / 1e9, diverged)
+
+
+def dissipation_error(fine: FineRun, coarse: CoarseRun) -> float:
+    """Relative L2 error of -dk/dt over the fine run's time grid (inf if the
+    coarse run diverged before the end)."""
+    if coarse.diverged_at is not None or len(coarse.times) < len(fine.times):
+        return math.inf
+    ef = -np.gradient(fine.k_filtered, fine.times)
+    ec = -np.gradient(coarse.k[:len(fine.times)], coarse.times[:len(fine.times)])
+    return float(np.linalg.norm(ec - ef) / np.linalg.norm(ef))
+
+
+def experiment(n_fine: int, factor: int, train_re, test_re: float, *, t_end: float = 10.0, steps: int = 2000,
+               batch: int = 8192, samples_per_snapshot: int = 200_000, seed: int = 0) -> dict:
+    """Fine runs at train_re (and test_re), training, and the three coarse
+    runs at test_re; returns a JSON-able summary."""
+    import torch
+    n_c = n_fine // factor
+    fines = {}
+    for re in sorted(set(list(train_re) + [test_re])):
+        fines[re] = fine_run(n_fine, re, factor, t_end=t_end, samples_per_snapshot=samples_per_snapshot,
+                             seed=seed + int(re))
+    X = torch.cat([fines[re].X for re in train_re])
+    y = torch.cat([fines[re].y for re in train_re])
+    t0 = time.perf_counter()
+    trained = train(X, y, steps=steps, batch=batch, seed=seed)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    runs = {c: coarse_run(n_c, test_re, c, trained, t_end=t_end) for c in ("bgk", "smagorinsky", "mlp")}
+    ref = fines[test_re]
+    return {
+        "n_fine": n_fine, "n_coarse": n_c, "factor": factor, "train_re": list(train_re), "test_re": test_re,
+        "t_end_tc": t_end, "train_samples": int(X.shape[0]), "train_steps": steps, "batch": batch,
+        "train_seconds": t_train, "loss_first_last": [trained.losses[0][1], trained.losses[-1][1]],
+        "target_mean": float(y.mean()),
+        "fine_glups": {str(re): fines[re].glups for re in fines},
+        "fine_diverged": {str(re): fines[re].diverged_at for re in fines},
+        "coarse": {c: {"dissipation_rel_l2": dissipation_error(ref, r), "glups": r.glups,
+                       "diverged_at_tc": r.diverged_at} for c, r in runs.items()},
+    }
+
+
+def main(argv=None):  # pragma: no cover - GPU workflow entry point
+    import argparse
+    ap = argparse.ArgumentParser(description="learned-closure experiment on the 3D Taylor-Green vortex")
+    ap.add_argument("--n-fine", type=int, default=512)
+    ap.add_argument("--factor", type=int, default=4)
+    ap.add_argument("--t-end", type=float, default=10.0)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--held-out", action="store_true", help="train on Re 800 and 3200, test on 1600")
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    train_re = (800.0, 3200.0) if a.held_out else (800.0, 1600.0, 3200.0)
+    res = experiment(a.n_fine, a.factor, train_re, 1600.0, t_end=a.t_end, steps=a.steps)
+    text = json.dumps(res, indent=1)
+    print(text)
+    if a.out:
+        with open(a.out, "w") as fh:
+            fh.write(text)
+    return 0
+
+
+if __name__ == "__main__":  # pragma: no cover
+    sys.exit(main())

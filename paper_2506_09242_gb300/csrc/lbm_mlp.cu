@@ -275,9 +275,42 @@ __global__ void k_coarse_samples(const double *__restrict__ rho, const double *_
     }
 }
 
+// Box filter: out[c][coarse cell] = mean of in[c] over its f^3 fine nodes.
+__global__ void k_box_filter(const double *__restrict__ in, int ncomp, int nx, int ny, int nz, int f,
+                             double *__restrict__ out)
+{
+    const int cnx = nx / f, cny = ny / f, cnz = nz / f;
+    const long long Nc = (long long)cnx * cny * cnz, N = (long long)nx * ny * nz;
+    const double inv = 1.0 / ((double)f * f * f);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < Nc * ncomp;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long comp = e / Nc, c = e % Nc;
+        const int cx = (int)(c % cnx), cy = (int)((c / cnx) % cny), cz = (int)(c / ((long long)cnx * cny));
+        double acc = 0.0;
+        for (int dz = 0; dz < f; ++dz)
+            for (int dy = 0; dy < f; ++dy)
+                for (int dx = 0; dx < f; ++dx)
+                    acc += in[comp * N + (cx * f + dx) + (long long)nx * ((cy * f + dy) + (long long)ny * (cz * f + dz))];
+        out[comp * Nc + c] = acc * inv;
+    }
+}
+
 }  // namespace
 
 extern "C" {
+
+lbm_status lbm_box_filter(const double *in, int ncomp, int nx, int ny, int nz, int factor, double *out, void *stream)
+{
+    if (!in || !out) return fail(LBM_ERR_ARG, "lbm_box_filter: NULL argument");
+    if (ncomp < 1 || factor < 1 || nx < factor || ny < factor || nz < factor || nx % factor || ny % factor ||
+        nz % factor)
+        return fail(LBM_ERR_ARG, "lbm_box_filter: sizes must be positive multiples of factor, ncomp >= 1");
+    const long long work = (long long)(nx / factor) * (ny / factor) * (nz / factor) * ncomp;
+    long long blocks = (work + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_box_filter<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(in, ncomp, nx, ny, nz, factor, out);
+    return launched("lbm_box_filter");
+}
 
 lbm_status lbm_mlp_forward(const float *params, const float *norm, const float *x, int n, float *dtau, void *stream)
 {

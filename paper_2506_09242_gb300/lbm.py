@@ -104,6 +104,7 @@ SIGNATURES = {
     "lbm_mlp_loss_grad": (_I, [_P, _P, _P, _P, _I, _P, _P, _P, _SZ, _P]),
     "lbm_mlp_adam": (_I, [_P, _P, _P, _P, _I, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P]),
     "lbm_coarse_samples": (_I, [_P, _P, _I, _I, _I, _I, _D, _P, _P, _P]),
+    "lbm_box_filter": (_I, [_P, _I, _I, _I, _I, _I, _P, _P]),
     "lbm_reduce_noalloc": (_I, [_P, _I, _I, _I, _I, _I, _P, ctypes.POINTER(Params), _P, ctypes.POINTER(Reduction)]),
 }
 
@@ -455,3 +456,16 @@ def coarse_samples(rho, u, factor, tau0):
     _check(load().lbm_coarse_samples(_dev(rho, "float64"), _dev(u, "float64"), nx, ny, nz, int(factor), float(tau0),
                                      _dev(X, "float32"), _dev(y, "float32"), _stream()))
     return X, y
+
+
+def box_filter(field, factor):
+    """Box-filtered copy of a device FP64 field of shape (c, nz, ny, nx) or
+    (nz, ny, nx)."""
+    import torch
+    squeeze = field.dim() == 3
+    f4 = field.unsqueeze(0) if squeeze else field
+    c, nz, ny, nx = f4.shape
+    out = torch.empty((c, nz // factor, ny // factor, nx // factor), dtype=torch.float64, device=field.device)
+    _check(load().lbm_box_filter(_dev(f4.contiguous(), "float64"), c, nx, ny, nz, int(factor), _dev(out, "float64"),
+                                 _stream()))
+    return out[0] if squeeze else out
