@@ -66,8 +66,14 @@ def tgv_fields(n: int):
     return _FIELDS[n]
 
 
-def make_workload(name: str, dtype: str):
-    """Returns (lattice, fields, description) with the lattice initialised."""
+CLOSURES = ("bgk", "smagorinsky", "mlp")
+
+
+def make_workload(name: str, dtype: str, closure: str = "bgk"):
+    """Returns (lattice, fields, description) with the lattice initialised.
+    closure "mlp" installs seeded random network weights: the cost of the
+    learned closure does not depend on the weight values."""
+    import numpy as np
     import lbm_inputs as inp
     from paper_2506_09242_gb300 import lbm
 
@@ -76,21 +82,27 @@ def make_workload(name: str, dtype: str):
         raise SystemExit(f"unknown workload {name}")
     kind, n, Q = m.group(1), int(m.group(2)), int(m.group(3))
     lat = lbm.Lattice(n, n, n, Q, dtype)
+    ckind = {"bgk": lbm.CLOSURE_BGK, "smagorinsky": lbm.CLOSURE_SMAGORINSKY, "mlp": lbm.CLOSURE_MLP}[closure]
+    if closure == "mlp":
+        norm = np.concatenate([np.zeros(6), [1.0], np.full(6, 1e-3), [0.01], [1e-4, 0.0]])
+        lat.set_closure_weights(inp.mlp_init(0).astype(np.float32), norm.astype(np.float32))
     if kind == "tgv":
         tau = tgv_tau(n, 0.04, 1600.0)
-        lat.set_params(tau)
+        lat.set_params(tau, closure=ckind, cs_smag=0.1)
         rho, u = tgv_fields(n)
         desc = {"workload": f"tgv3d_{n}_d3q{Q}_{dtype}", "problem": "periodic 3D Taylor-Green vortex",
                 "u0": 0.04, "Re": 1600, "tau": tau}
     else:
         tau = 0.5 + 3.0 * 0.1 * n / 1000.0
         lat.set_tags(inp.cavity_tags(n))
-        lat.set_params(tau, wall_u=[(0.1, 0.0, 0.0)])
+        lat.set_params(tau, wall_u=[(0.1, 0.0, 0.0)], closure=ckind, cs_smag=0.1)
         rho, u = None, None
         desc = {"workload": f"cavity_{n}_d3q{Q}_{dtype}", "problem": "lid-driven cavity, Ladd lid",
                 "u_lid": 0.1, "Re": 1000, "tau": tau}
     lat.init_equilibrium(rho, u)
-    desc.update({"lattice": f"D3Q{Q}", "storage": dtype, "nx": n, "ny": n, "nz": n})
+    desc.update({"lattice": f"D3Q{Q}", "storage": dtype, "nx": n, "ny": n, "nz": n, "closure": closure})
+    if closure != "bgk":
+        desc["workload"] += f"_{closure}"
     return lat, (rho, u), desc
 
 
@@ -334,7 +346,7 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    lat, fields, desc = make_workload(args.workload, args.dtype)
+    lat, fields, desc = make_workload(args.workload, args.dtype, args.closure)
     Q = int(desc["lattice"][3:])
     cells = lat.N
     sampler = ClockSampler(local)
@@ -365,11 +377,14 @@ def run_ours(args):
     errors = None
     cpu = None
     if rank == 0 and not args.no_extras:
-        for wl, dt in (("tgv512_d3q19", "f16"), ("tgv512_d3q19", "bf16"), ("cavity256_d3q19", "f32"),
-                       ("tgv512_d3q27", "f32"), ("tgv512_d3q27", "f16")):
-            if (wl, dt) == (args.workload, args.dtype):
+        for wl, dt, cl in (("tgv512_d3q19", "f16", "bgk"), ("tgv512_d3q19", "bf16", "bgk"),
+                           ("cavity256_d3q19", "f32", "bgk"), ("tgv512_d3q27", "f32", "bgk"),
+                           ("tgv512_d3q27", "f16", "bgk"), ("tgv512_d3q19", "f32", "smagorinsky"),
+                           ("tgv512_d3q19", "f32", "mlp"), ("tgv128_d3q19", "f32", "bgk"),
+                           ("tgv128_d3q19", "f32", "mlp")):
+            if (wl, dt, cl) == (args.workload, args.dtype, args.closure):
                 continue
-            v, _, d = make_workload(wl, dt)
+            v, _, d = make_workload(wl, dt, cl)
             tms, kms, _ = time_lattice(v, 5, 3, args.inner)
             q = int(d["lattice"][3:])
             ach = 2 * q * SIZE[dt] * v.N / (kms * 1e-3) / 1e9
@@ -421,6 +436,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="tgv512_d3q19")
     ap.add_argument("--dtype", default="f32", choices=sorted(SIZE))
+    ap.add_argument("--closure", default="bgk", choices=CLOSURES)
     ap.add_argument("--inner", type=int, default=20, help="lattice steps per benchmark step")
     ap.add_argument("--ref-n", type=int, default=64, help="lattice size of the oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip variants, error table and CPU baseline")

@@ -28,6 +28,7 @@ struct lbm_ctx {
     double *red_out = nullptr;  // kRedSlots final sums
     unsigned long long *census_dev = nullptr;  // LBM_NTAGS + 1 counters
     float *mlp_params = nullptr;  // closure weights (LBM_MLP_NPARAM) + normalisation (LBM_MLP_NNORM)
+    void *mlp_image = nullptr;    // the network packed for the collide kernel
     cudaStream_t stream = nullptr;
     lbm_allocator alloc{};
     bool has_alloc = false;
@@ -106,8 +107,7 @@ Launch make_launch(lbm_ctx *ctx)
     L.tags = ctx->tags;
     L.general = ctx->general;
     L.closure = ctx->params.closure;
-    L.mlp_params = ctx->mlp_params;
-    L.mlp_norm = ctx->mlp_params ? ctx->mlp_params + LBM_MLP_NPARAM : nullptr;
+    L.mlp_image = ctx->mlp_image;
     L.stream = ctx->stream;
     return L;
 }
@@ -271,6 +271,7 @@ lbm_status lbm_destroy(lbm_ctx *ctx)
     dev_free(ctx, ctx->red_out, sizeof(double) * kRedSlots);
     dev_free(ctx, ctx->census_dev, sizeof(unsigned long long) * (LBM_NTAGS + 1));
     dev_free(ctx, ctx->mlp_params, sizeof(float) * (LBM_MLP_NPARAM + LBM_MLP_NNORM));
+    dev_free(ctx, ctx->mlp_image, mlp_image_bytes());
     delete ctx;
     return LBM_OK;
 }
@@ -428,7 +429,7 @@ lbm_status lbm_step(lbm_ctx *ctx, int n)
 {
     if (!ctx) return fail(ctx, LBM_ERR_ARG, "NULL context");
     if (n < 0) return fail(ctx, LBM_ERR_ARG, "n must be >= 0");
-    if (ctx->params.closure == LBM_CLOSURE_MLP && !ctx->mlp_params)
+    if (ctx->params.closure == LBM_CLOSURE_MLP && !ctx->mlp_image)
         return fail(ctx, LBM_ERR_STATE, "MLP closure selected but no weights were set (lbm_set_closure_weights)");
     for (int k = 0; k < n; ++k) {
         Launch L = make_launch(ctx);
@@ -660,9 +661,12 @@ lbm_status lbm_set_closure_weights(lbm_ctx *ctx, const float *params, const floa
     if (!(src_n[14] >= 0.f)) return fail(ctx, LBM_ERR_ARG, "out_scale must be >= 0");
     if (!ctx->mlp_params) {
         ctx->mlp_params = (float *)dev_alloc(ctx, sizeof(float) * (LBM_MLP_NPARAM + LBM_MLP_NNORM));
-        if (!ctx->mlp_params) return fail(ctx, LBM_ERR_OOM, "closure weight allocation failed");
+        ctx->mlp_image = dev_alloc(ctx, mlp_image_bytes());
+        if (!ctx->mlp_params || !ctx->mlp_image) return fail(ctx, LBM_ERR_OOM, "closure weight allocation failed");
     }
     CUDA_TRY(ctx, cudaMemcpyAsync(ctx->mlp_params, host, sizeof host, cudaMemcpyHostToDevice, ctx->stream), "weights upload");
+    CUDA_TRY(ctx, launch_mlp_pack(ctx->mlp_params, ctx->mlp_params + LBM_MLP_NPARAM, ctx->mlp_image, ctx->stream),
+             "weights packing");
     return sync(ctx);
 }
 

@@ -118,8 +118,7 @@ struct Launch {
     const uint8_t *tags;      // internal padded tags
     bool general;             // tags present (not all FLUID)
     int closure;
-    const float *mlp_params;  // device FP32 closure parameters (closure 2)
-    const float *mlp_norm;    // device normalisation vector (closure 2)
+    const void *mlp_image;    // device packed closure network (MlpSmem, closure 2)
     cudaStream_t stream;
 };
 
@@ -145,6 +144,8 @@ cudaError_t launch_sphere_cover(int nx, int ny, int nz, const int *centres, cons
 cudaError_t launch_sphere_histogram(long long N, const uint32_t *cover, uint32_t *count, cudaStream_t s);
 cudaError_t launch_sphere_tags(long long N, const uint32_t *cover, uint32_t used, uint8_t pore_tag, uint8_t *tags,
                                cudaStream_t s);
+cudaError_t launch_mlp_pack(const float *params, const float *norm, void *image, cudaStream_t s);
+size_t mlp_image_bytes();
 cudaError_t launch_enstrophy(bool fp64, int nx, int ny, int nz, const double *u, double *partials, int nblocks,
                              double *out, cudaStream_t s);
 

@@ -246,15 +246,14 @@ __global__ void __launch_bounds__(kStepThreads)
 template <int Q, typename S, bool GENERAL>
 __global__ void __launch_bounds__(kStepThreads)
     k_collide_stream_mlp(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ tags, Grid g,
-                         KParams<typename Store<S>::T> p, const float *__restrict__ mlp_params,
-                         const float *__restrict__ mlp_norm)
+                         KParams<typename Store<S>::T> p, const MlpSmem *__restrict__ mlp_image)
 {
     using T = typename Store<S>::T;
     using St = Store<S>;
     __shared__ MlpSmem W;
     __shared__ uint32_t stage[kStepThreads / 32][32 * 8];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    load_mlp_smem(mlp_params, mlp_norm, W, tid, blockDim.x * blockDim.y);
+    copy_mlp_image(mlp_image, W, tid, blockDim.x * blockDim.y);
     __syncthreads();
 
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -724,8 +723,9 @@ cudaError_t step_closure(const Launch &L, const KParams<typename Store<S>::T> &k
     const S *A = (const S *)L.A;
     S *B = (S *)L.B;
     if (L.closure == LBM_CLOSURE_MLP) {
-        if (!L.mlp_params || !L.mlp_norm) return cudaErrorInvalidValue;
-        k_collide_stream_mlp<Q, S, GEN><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, L.mlp_params, L.mlp_norm);
+        if (!L.mlp_image) return cudaErrorInvalidValue;
+        k_collide_stream_mlp<Q, S, GEN>
+            <<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, (const MlpSmem *)L.mlp_image);
         return cudaGetLastError();
     }
     if constexpr (use_pairs<S>()) {

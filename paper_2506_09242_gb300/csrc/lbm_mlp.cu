@@ -295,7 +295,23 @@ __global__ void k_box_filter(const double *__restrict__ in, int ncomp, int nx, i
     }
 }
 
+// Packs FP32 parameters once into the shared-memory image the collide kernel
+// copies (one block).
+__global__ void k_mlp_pack(const float *__restrict__ P, const float *__restrict__ norm, MlpSmem *__restrict__ img)
+{
+    load_mlp_smem(P, norm, *img, threadIdx.x, blockDim.x);
+}
+
 }  // namespace
+
+namespace lbm {
+size_t mlp_image_bytes() { return sizeof(MlpSmem); }
+cudaError_t launch_mlp_pack(const float *params, const float *norm, void *image, cudaStream_t s)
+{
+    k_mlp_pack<<<1, 128, 0, s>>>(params, norm, (MlpSmem *)image);
+    return cudaGetLastError();
+}
+}  // namespace lbm
 
 extern "C" {
 

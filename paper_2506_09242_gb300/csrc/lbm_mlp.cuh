@@ -19,13 +19,24 @@ namespace lbm {
 
 // Shared-memory copy of the network, packed for the mma fragments: BF16
 // pairs (k, k+1) of each output row, inputs padded from 7 to 16.
-struct MlpSmem {
+struct __align__(16) MlpSmem {
     uint32_t W1p[kMlpH][8];   // row n: pairs of W1[n][0..15] (cols 7..15 zero)
     uint32_t W2p[kMlpH][16];  // row n: pairs of W2[n][0..31]
     float b1[kMlpH], b2[kMlpH], w3[kMlpH];
     float b3, out_scale;
     float mean[kMlpIn], inv_std[kMlpIn];
 };
+static_assert(sizeof(MlpSmem) % 16 == 0, "the packed network is copied in 16-byte words");
+
+// Copies a packed network (built once by load_mlp_smem into global memory)
+// into shared memory with 16-byte loads.  All threads call it; the caller
+// synchronises after.
+__device__ __forceinline__ void copy_mlp_image(const MlpSmem *__restrict__ img, MlpSmem &sm, int tid, int nthreads)
+{
+    const uint4 *src = reinterpret_cast<const uint4 *>(img);
+    uint4 *dst = reinterpret_cast<uint4 *>(&sm);
+    for (int e = tid; e < (int)(sizeof(MlpSmem) / 16); e += nthreads) dst[e] = __ldg(src + e);
+}
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
@@ -84,15 +95,30 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.f + __expf(-z)); }
+// SiLU(z) = z sigmoid(z) = (z/2) (1 + tanh(z/2)), with the hardware tanh
+// approximation (one MUFU operation; relative error about 2^-11, below the
+// BF16 rounding that follows in the first layer).
+__device__ __forceinline__ float tanh_approx(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float silu_f(float z)
+{
+    const float hz = 0.5f * z;
+    return fmaf(hz, tanh_approx(hz), hz);
+}
 __device__ __forceinline__ float softplus_f(float y) { return y > 20.f ? y : log1pf(__expf(y)); }
 
 // The network on 32 nodes at once, one per lane (a warp-collective call:
 // all 32 lanes must take part).  stage: 32 x 8 words of per-warp shared
-// memory.  Returns this lane's dtau.  Two 16-node tiles; per tile layer 1 is
-// 4 mma (N = 32 hidden in 4 tiles of 8, K = 16 padded inputs), layer 2 is 8
-// mma (K = 32 in 2 steps, the layer-1 accumulators re-packed in place as the
-// A fragments), layer 3 a dot product reduced over each lane quad.
+// memory.  Returns this lane's dtau.  The 32 nodes form two 16-row tiles that
+// share every weight fragment: layer 1 is 4 mma per tile (N = 32 hidden in 4
+// tiles of 8, K = 16 padded inputs), layer 2 is 8 mma per tile (K = 32 in 2
+// steps, the layer-1 results re-packed in registers as the A fragments),
+// layer 3 a dot product reduced over each lane quad.  Accumulators start at
+// the biases.
 __device__ __forceinline__ float mlp_warp_dtau(const MlpSmem &W, uint32_t *stage, const float (&x)[kMlpIn],
                                                unsigned lane)
 {
@@ -106,54 +132,64 @@ __device__ __forceinline__ float mlp_warp_dtau(const MlpSmem &W, uint32_t *stage
     row[3] = pack_bf16(xn[6], 0.f);
     __syncwarp();
     const unsigned g = lane >> 2, q = lane & 3;
-    float yq[2][2];
+    // A fragments of the inputs for both tiles (columns 8..15 are zero).
+    uint32_t a0[2], a1[2];
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
-        // A fragment of the inputs: columns 8..15 are padding (zero).
-        const uint32_t a0 = stage[(16 * t + g) * 8 + q];
-        const uint32_t a1 = stage[(16 * t + g + 8) * 8 + q];
-        float h1[4][4];
+        a0[t] = stage[(16 * t + g) * 8 + q];
+        a1[t] = stage[(16 * t + g + 8) * 8 + q];
+    }
+    // Layer 1, re-packed as layer-2 A fragments a2[t][k-step][4].
+    uint32_t a2[2][2][4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float c[4] = {0.f, 0.f, 0.f, 0.f};
-            mma_bf16(c, a0, a1, 0u, 0u, W.W1p[8 * j + g][q], W.W1p[8 * j + g][4 + q]);
-            const int col = 8 * j + 2 * q;
-            h1[j][0] = silu_f(c[0] + W.b1[col]);
-            h1[j][1] = silu_f(c[1] + W.b1[col + 1]);
-            h1[j][2] = silu_f(c[2] + W.b1[col]);
-            h1[j][3] = silu_f(c[3] + W.b1[col + 1]);
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t b0 = W.W1p[8 * j + g][q], b1 = W.W1p[8 * j + g][4 + q];
+        const int col = 8 * j + 2 * q;
+        const float bias0 = W.b1[col], bias1 = W.b1[col + 1];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            float c[4] = {bias0, bias1, bias0, bias1};
+            mma_bf16(c, a0[t], a1[t], 0u, 0u, b0, b1);
+            a2[t][j >> 1][(j & 1) * 2] = pack_bf16(silu_f(c[0]), silu_f(c[1]));
+            a2[t][j >> 1][(j & 1) * 2 + 1] = pack_bf16(silu_f(c[2]), silu_f(c[3]));
         }
-        uint32_t a2[2][4];
+    }
+    // Layer 2 and the output dot product.
+    float pg[2] = {0.f, 0.f}, pg8[2] = {0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int col = 8 * j + 2 * q;
+        const float bias0 = W.b2[col], bias1 = W.b2[col + 1];
+        const float w0 = W.w3[col], w1 = W.w3[col + 1];
+        float c[2][4];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            c[t][0] = c[t][2] = bias0;
+            c[t][1] = c[t][3] = bias1;
+        }
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            a2[s][0] = pack_bf16(h1[2 * s][0], h1[2 * s][1]);
-            a2[s][1] = pack_bf16(h1[2 * s][2], h1[2 * s][3]);
-            a2[s][2] = pack_bf16(h1[2 * s + 1][0], h1[2 * s + 1][1]);
-            a2[s][3] = pack_bf16(h1[2 * s + 1][2], h1[2 * s + 1][3]);
-        }
-        float pg = 0.f, pg8 = 0.f;
+            const uint32_t b0 = W.W2p[8 * j + g][8 * s + q], b1 = W.W2p[8 * j + g][8 * s + 4 + q];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int s = 0; s < 2; ++s)
-                mma_bf16(c, a2[s][0], a2[s][1], a2[s][2], a2[s][3], W.W2p[8 * j + g][8 * s + q],
-                         W.W2p[8 * j + g][8 * s + 4 + q]);
-            const int col = 8 * j + 2 * q;
-            pg += silu_f(c[0] + W.b2[col]) * W.w3[col] + silu_f(c[1] + W.b2[col + 1]) * W.w3[col + 1];
-            pg8 += silu_f(c[2] + W.b2[col]) * W.w3[col] + silu_f(c[3] + W.b2[col + 1]) * W.w3[col + 1];
+            for (int t = 0; t < 2; ++t) mma_bf16(c[t], a2[t][s][0], a2[t][s][1], a2[t][s][2], a2[t][s][3], b0, b1);
         }
-        pg += __shfl_xor_sync(0xffffffffu, pg, 1);
-        pg += __shfl_xor_sync(0xffffffffu, pg, 2);
-        pg8 += __shfl_xor_sync(0xffffffffu, pg8, 1);
-        pg8 += __shfl_xor_sync(0xffffffffu, pg8, 2);
-        yq[t][0] = pg;
-        yq[t][1] = pg8;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            pg[t] = fmaf(silu_f(c[t][0]), w0, fmaf(silu_f(c[t][1]), w1, pg[t]));
+            pg8[t] = fmaf(silu_f(c[t][2]), w0, fmaf(silu_f(c[t][3]), w1, pg8[t]));
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        pg[t] += __shfl_xor_sync(0xffffffffu, pg[t], 1);
+        pg[t] += __shfl_xor_sync(0xffffffffu, pg[t], 2);
+        pg8[t] += __shfl_xor_sync(0xffffffffu, pg8[t], 1);
+        pg8[t] += __shfl_xor_sync(0xffffffffu, pg8[t], 2);
     }
     // Row r of tile t lives in lane quad (r mod 8); hand it to lane 16 t + r.
     const unsigned r = lane & 15, src = 4 * (r & 7);
-    const float v00 = __shfl_sync(0xffffffffu, yq[0][0], src), v01 = __shfl_sync(0xffffffffu, yq[0][1], src);
-    const float v10 = __shfl_sync(0xffffffffu, yq[1][0], src), v11 = __shfl_sync(0xffffffffu, yq[1][1], src);
+    const float v00 = __shfl_sync(0xffffffffu, pg[0], src), v01 = __shfl_sync(0xffffffffu, pg8[0], src);
+    const float v10 = __shfl_sync(0xffffffffu, pg[1], src), v11 = __shfl_sync(0xffffffffu, pg8[1], src);
     const float y = (lane < 16 ? (r < 8 ? v00 : v01) : (r < 8 ? v10 : v11)) + W.b3;
     __syncwarp();  // stage may be rewritten by the caller after this
     return W.out_scale * softplus_f(y);
