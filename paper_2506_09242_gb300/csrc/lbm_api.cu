@@ -29,6 +29,9 @@ struct lbm_ctx {
     unsigned long long *census_dev = nullptr;  // LBM_NTAGS + 1 counters
     float *mlp_params = nullptr;  // closure weights (LBM_MLP_NPARAM) + normalisation (LBM_MLP_NNORM)
     void *mlp_image = nullptr;    // the network packed for the collide kernel
+    int *fluid_list = nullptr;    // fluid-node list (mostly-wall lattices), else NULL
+    uint32_t *fluid_mask = nullptr;
+    long long n_list = 0;
     cudaStream_t stream = nullptr;
     lbm_allocator alloc{};
     bool has_alloc = false;
@@ -108,6 +111,9 @@ Launch make_launch(lbm_ctx *ctx)
     L.general = ctx->general;
     L.closure = ctx->params.closure;
     L.mlp_image = ctx->mlp_image;
+    L.fluid_list = ctx->fluid_list;
+    L.fluid_mask = ctx->fluid_mask;
+    L.n_list = ctx->n_list;
     L.stream = ctx->stream;
     return L;
 }
@@ -252,6 +258,44 @@ cudaError_t launch_prepare_tags(int Q, const Grid &g, const uint8_t *user, uint8
 
 }  // namespace lbm
 
+// (Re)builds the fluid-node list after the tags changed, or drops it when the
+// lattice is mostly fluid.  Row counts are scanned on the host.
+static lbm_status build_fluid_list(lbm_ctx *ctx, bool wanted)
+{
+    dev_free(ctx, ctx->fluid_list, sizeof(int) * (size_t)ctx->n_list);
+    dev_free(ctx, ctx->fluid_mask, sizeof(uint32_t) * (size_t)ctx->n_list);
+    ctx->fluid_list = nullptr;
+    ctx->fluid_mask = nullptr;
+    ctx->n_list = 0;
+    if (!wanted) return LBM_OK;
+    const size_t rows = (size_t)ctx->g.nz * ctx->g.ny;
+    Tmp count(ctx, sizeof(int) * rows);
+    if (!count.p) return fail(ctx, LBM_ERR_OOM, "fluid-list allocation failed");
+    CUDA_TRY(ctx, launch_fluid_count(ctx->g, ctx->tags, (int *)count.p, ctx->stream), "fluid count");
+    std::vector<int> h(rows);
+    CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), count.p, sizeof(int) * rows, cudaMemcpyDeviceToHost, ctx->stream),
+             "fluid count copy");
+    lbm_status s = sync(ctx);
+    if (s != LBM_OK) return s;
+    long long total = 0;
+    for (size_t r = 0; r < rows; ++r) {  // exclusive prefix sum
+        const int c = h[r];
+        h[r] = (int)total;
+        total += c;
+    }
+    if (total == 0) return LBM_OK;
+    ctx->fluid_list = (int *)dev_alloc(ctx, sizeof(int) * (size_t)total);
+    ctx->fluid_mask = (uint32_t *)dev_alloc(ctx, sizeof(uint32_t) * (size_t)total);
+    ctx->n_list = total;
+    if (!ctx->fluid_list || !ctx->fluid_mask) return fail(ctx, LBM_ERR_OOM, "fluid-list allocation failed");
+    CUDA_TRY(ctx, cudaMemcpyAsync(count.p, h.data(), sizeof(int) * rows, cudaMemcpyHostToDevice, ctx->stream),
+             "fluid start copy");
+    CUDA_TRY(ctx, launch_fluid_scatter(ctx->Q, ctx->g, ctx->tags, (const int *)count.p, ctx->fluid_list, ctx->fluid_mask,
+                                       ctx->stream),
+             "fluid scatter");
+    return sync(ctx);
+}
+
 // ---------------------------------------------------------------------------
 // C ABI.
 // ---------------------------------------------------------------------------
@@ -272,6 +316,8 @@ lbm_status lbm_destroy(lbm_ctx *ctx)
     dev_free(ctx, ctx->census_dev, sizeof(unsigned long long) * (LBM_NTAGS + 1));
     dev_free(ctx, ctx->mlp_params, sizeof(float) * (LBM_MLP_NPARAM + LBM_MLP_NNORM));
     dev_free(ctx, ctx->mlp_image, mlp_image_bytes());
+    dev_free(ctx, ctx->fluid_list, sizeof(int) * (size_t)ctx->n_list);
+    dev_free(ctx, ctx->fluid_mask, sizeof(uint32_t) * (size_t)ctx->n_list);
     delete ctx;
     return LBM_OK;
 }
@@ -370,11 +416,15 @@ lbm_status lbm_set_tags(lbm_ctx *ctx, const uint8_t *tags, int on_device)
     CUDA_TRY(ctx, cudaMemcpyAsync(ctx->tags, scratch.p, (size_t)ctx->g.sN, cudaMemcpyDeviceToDevice, ctx->stream),
              "tag install");
     bool general = false;
+    long long walls = 0;
     for (int k = 0; k < LBM_NTAGS; ++k) {
         ctx->census[k] = (long long)c[k];
         if (k != LBM_TAG_FLUID && c[k]) general = true;
+        if (is_wall_tag((unsigned)k)) walls += (long long)c[k];
     }
     ctx->general = general;
+    s = build_fluid_list(ctx, walls > kListWallFraction * (double)ctx->g.N);
+    if (s != LBM_OK) return s;
     return sync(ctx);
 }
 

@@ -76,6 +76,12 @@ template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat16 from_f64(double v) { return __float2bfloat16_rn((float)v); }
 };
 
+// Fluid-node list (lattices that are mostly wall): link mask of each listed
+// node, bit i set when the pull source of direction i is SOLID or WALL.
+constexpr uint32_t kListForced = 1u << 30;   // the node carries the body force
+constexpr uint32_t kListAnyWall = 1u << 31;  // some source is a moving wall
+constexpr double kListWallFraction = 0.3;    // use the list above this wall fraction
+
 // Internal tag byte: the user tag in the low 7 bits, bit 7 set on fluid
 // nodes that have a SOLID or WALL node among their Q neighbours.
 constexpr uint8_t kNearWall = 0x80;
@@ -119,6 +125,9 @@ struct Launch {
     bool general;             // tags present (not all FLUID)
     int closure;
     const void *mlp_image;    // device packed closure network (MlpSmem, closure 2)
+    const int *fluid_list;    // padded offsets of the fluid nodes, or NULL (dense sweep)
+    const uint32_t *fluid_mask;
+    long long n_list;
     cudaStream_t stream;
 };
 
@@ -137,6 +146,11 @@ template <typename S> cudaError_t launch_set_pop(const Launch &L, int i, const d
 cudaError_t launch_prepare_tags(int Q, const Grid &g, const uint8_t *user_tags, uint8_t *tags,
                                 unsigned long long *census, cudaStream_t s);
 cudaError_t launch_gather_tags(const Grid &g, const uint8_t *tags, uint8_t *out, cudaStream_t s);
+
+// Fluid-node list (lbm_sparse.cu).
+cudaError_t launch_fluid_count(const Grid &g, const uint8_t *tags, int *count, cudaStream_t s);
+cudaError_t launch_fluid_scatter(int Q, const Grid &g, const uint8_t *tags, const int *start, int *list,
+                                 uint32_t *mask, cudaStream_t s);
 
 // Porous-medium generator and enstrophy diagnostic (lbm_diag.cu).
 cudaError_t launch_sphere_cover(int nx, int ny, int nz, const int *centres, const double *radii, int n,

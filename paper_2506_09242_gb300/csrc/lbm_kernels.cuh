@@ -237,6 +237,61 @@ __global__ void __launch_bounds__(kStepThreads)
 }
 
 // ---------------------------------------------------------------------------
+// The step over a list of fluid nodes (lattices that are mostly wall, e.g.
+// porous media): one thread per listed node, solid nodes are never visited.
+// Each node's link mask says which pull sources are walls, so a direction
+// costs one load either way (the neighbour's population, or the node's own
+// opposite population for bounce-back); tags are read only for links to a
+// moving wall.
+// ---------------------------------------------------------------------------
+template <int Q, typename T>
+__device__ __forceinline__ T wall_term(int i, unsigned ts, const KParams<T> &p)
+{
+    T ux = T(0), uy = T(0), uz = T(0);
+#pragma unroll
+    for (int k = 0; k < LBM_NWALLS; ++k)
+        if (ts == (unsigned)(LBM_TAG_WALL0 + k)) {
+            ux = p.wall6[k][0];
+            uy = p.wall6[k][1];
+            uz = p.wall6[k][2];
+        }
+    return wgt<T>(Q, i) * (T(cvel(i, 0)) * ux + T(cvel(i, 1)) * uy + T(cvel(i, 2)) * uz);
+}
+
+template <int Q, typename S, int CLOSURE>
+__global__ void __launch_bounds__(kStepThreads)
+    k_collide_stream_list(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ tags, Grid g,
+                          KParams<typename Store<S>::T> p, const int *__restrict__ list,
+                          const uint32_t *__restrict__ mask, long long n)
+{
+    using T = typename Store<S>::T;
+    using St = Store<S>;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int off = __ldg(list + t);
+    const uint32_t m = __ldg(mask + t);
+    const int r = off / g.px;
+    Nbr nb;
+    nb.init(g, off - r * g.px, r % g.ny, r / g.ny);
+    T h[Q];
+    h[0] = St::ld(A + nb.self);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const bool bb = (m >> i) & 1u;
+        const long long a = bb ? (long long)opp(i) * g.sN + nb.self : (long long)i * g.sN + nb.src(i);
+        T v = St::ld(A + a);
+        if (bb && (m & kListAnyWall)) {
+            const unsigned ts = tags[nb.src(i)] & kTagMask;
+            if (ts >= LBM_TAG_WALL0) v += wall_term<Q, T>(i, ts, p);
+        }
+        h[i] = v;
+    }
+    collide_node<Q, T, CLOSURE>(h, (m & kListForced) != 0u, p);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) St::st(B + (long long)i * g.sN + nb.self, h[i]);
+}
+
+// ---------------------------------------------------------------------------
 // The step with the learned closure: tau_eff = tau + dtau(Pi^neq, rho) per
 // node, the network evaluated by each warp on its 32 nodes as a BF16
 // tensor-core tile (mlp_warp_dtau).  Every lane of a warp takes part in the
@@ -744,11 +799,39 @@ cudaError_t step_closure(const Launch &L, const KParams<typename Store<S>::T> &k
     return cudaGetLastError();
 }
 
+template <int Q, typename S>
+cudaError_t step_list(const Launch &L, const KParams<typename Store<S>::T> &kp)
+{
+    const S *A = (const S *)L.A;
+    S *B = (S *)L.B;
+    const unsigned blocks = (unsigned)((L.n_list + kStepThreads - 1) / kStepThreads);
+    if (blocks == 0) return cudaSuccess;
+    switch (L.closure) {
+    case LBM_CLOSURE_BGK:
+        k_collide_stream_list<Q, S, LBM_CLOSURE_BGK>
+            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, L.tags, L.g, kp, L.fluid_list, L.fluid_mask, L.n_list);
+        break;
+    case LBM_CLOSURE_SMAGORINSKY:
+        k_collide_stream_list<Q, S, LBM_CLOSURE_SMAGORINSKY>
+            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, L.tags, L.g, kp, L.fluid_list, L.fluid_mask, L.n_list);
+        break;
+    case LBM_CLOSURE_STREAM_ONLY:
+        k_collide_stream_list<Q, S, LBM_CLOSURE_STREAM_ONLY>
+            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, L.tags, L.g, kp, L.fluid_list, L.fluid_mask, L.n_list);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <int Q, typename S> cudaError_t step_q(const Launch &L, const lbm_params &p)
 {
     dim3 grid, block;
     node_launch_shape(L.g, grid, block);
     const auto kp = make_kparams<typename Store<S>::T>(Q, p);
+    // Mostly-wall lattices walk the fluid-node list (the learned closure
+    // needs whole warps of consecutive nodes and keeps the dense sweep).
+    if (L.fluid_list && L.closure != LBM_CLOSURE_MLP) return step_list<Q, S>(L, kp);
     return L.general ? step_closure<Q, S, true>(L, kp, grid, block) : step_closure<Q, S, false>(L, kp, grid, block);
 }
 

@@ -1,0 +1,160 @@
+"""The reference workloads as library call sequences (no numerics in Python).
+
+- ``porous``: pore-scale flow through a random-sphere medium (the stand-in for
+  the Berea sandstone of Sec. 3.3): body force on pore nodes, bounce-back on
+  solids, run to steady state. Reports the permeability k = u_mean nu / g
+  (u_mean over all nodes, solid = 0) and GLUPS over fluid nodes only.
+- ``cavity``: lid-driven cavity of Sec. 3.2 (SOLID walls, Ladd lid).
+- ``tgv_precision``: the 3D Taylor-Green vortex of Sec. 3.1 with FP64, FP32,
+  FP16- and BF16-shifted storage. Records kinetic energy and enstrophy curves
+  and the velocity error against the FP64 run at chosen times.
+
+torch is used for device buffers and for differences of fields when
+evaluating errors.
+"""
+from __future__ import annotations
+
+import json
+import math
+import sys
+import time
+
+import numpy as np
+
+from . import lbm
+
+
+def _sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def porous(n: int = 400, *, seed: int = 2506, rmin: float = 4.0, rmax: float = 10.0, target: float = 0.2,
+           g: float = 1e-6, tau: float = 1.0, max_steps: int = 50_000, check_every: int = 1000, tol: float = 1e-6,
+           dtype: str = "f32") -> dict:
+    import lbm_inputs as inp
+    centres, radii = inp.sphere_list((n, n, n), seed=seed, rmin=rmin, rmax=rmax, count=100_000)
+    with lbm.Lattice(n, n, n, lbm.D3Q19, dtype) as lat:
+        used, por = lat.geometry_spheres(centres, radii, target, lbm.TAG_FORCED)
+        lat.set_params(tau, force=(g, 0.0, 0.0))
+        lat.init_equilibrium()
+        n_fluid = int(lat.census()[lbm.TAG_FORCED])
+        nu = (tau - 0.5) / 3.0
+        hist, steps, t_step, prev = [], 0, 0.0, None
+        converged = False
+        while steps < max_steps:
+            _sync()
+            t0 = time.perf_counter()
+            lat.step(check_every)
+            _sync()
+            t_step += time.perf_counter() - t0
+            steps += check_every
+            red = lat.reduce()
+            u_mean = red["vel"][0] / n ** 3
+            hist.append((steps, u_mean))
+            if prev is not None and abs(u_mean - prev) <= tol * abs(u_mean):
+                converged = True
+                break
+            prev = u_mean
+    k = u_mean * nu / g
+    return {"n": n, "spheres": used, "porosity": por, "fluid_nodes": n_fluid, "tau": tau, "g": g,
+            "steps": steps, "converged": converged, "u_mean": u_mean, "permeability_voxel2": k,
+            "glups_fluid": n_fluid * steps / t_step / 1e9, "glups_all_nodes": n ** 3 * steps / t_step / 1e9,
+            "history": hist[-5:]}
+
+
+def cavity(n: int = 256, *, re: float = 1000.0, u_lid: float = 0.1, steps: int = 10_000, dtype: str = "f32") -> dict:
+    import lbm_inputs as inp
+    tau = 0.5 + 3.0 * u_lid * n / re
+    with lbm.Lattice(n, n, n, lbm.D3Q19, dtype) as lat:
+        lat.set_tags(inp.cavity_tags(n))
+        lat.set_params(tau, wall_u=[(u_lid, 0.0, 0.0)])
+        lat.init_equilibrium()
+        n_fluid = int(lat.census()[lbm.TAG_FLUID])
+        _sync()
+        t0 = time.perf_counter()
+        lat.step(steps)
+        _sync()
+        dt = time.perf_counter() - t0
+        red = lat.reduce()
+        rho, u = lat.moments()
+    mid = n // 2
+    return {"n": n, "re": re, "tau": tau, "steps": steps, "t_c": steps * u_lid / n,
+            "glups_all_nodes": n ** 3 * steps / dt / 1e9, "glups_fluid": n_fluid * steps / dt / 1e9,
+            "ke_per_fluid_node": red["ke"] / red["n_fluid"], "umax": red["umax"],
+            "ux_centreline_z": u[0, :, mid, mid][:: max(1, n // 16)].tolist()}
+
+
+def tgv_precision(n: int = 512, Q: int = 27, *, dtypes=("f64", "f32", "f16", "bf16"), u0: float = 0.04,
+                  re: float = 1600.0, t_end: float = 10.0, every: float = 0.5, error_at=(1.0, 5.0, 10.0)) -> dict:
+    """Runs the TGV once per storage type (FP64 first) and compares each
+    velocity field with the FP64 one at the times in error_at."""
+    import torch
+    import lbm_inputs as inp
+    tau = 0.5 + 3.0 * u0 * (n / (2.0 * math.pi)) / re
+    spt = n / (2.0 * math.pi * u0)
+    rho, u = inp.tgv3d(n, u0)
+    ref_fields = {}
+    out = {"n": n, "Q": Q, "re": re, "u0": u0, "tau": tau, "steps_per_tc": spt, "runs": {}}
+    marks = sorted(set([round(j * every, 6) for j in range(int(round(t_end / every)) + 1)] + list(error_at)))
+    for dt in dtypes:
+        curves, errs = [], {}
+        t_step = 0.0
+        with lbm.Lattice(n, n, n, Q, dt) as lat:
+            lat.set_params(tau)
+            lat.init_equilibrium(rho, u)
+            uu = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
+            done = 0
+            for t in marks:
+                target = int(round(t * spt))
+                if target > done:
+                    _sync()
+                    t0 = time.perf_counter()
+                    lat.step(target - done)
+                    _sync()
+                    t_step += time.perf_counter() - t0
+                    done = target
+                try:
+                    red = lat.reduce()
+                except lbm.UnstableError:
+                    curves.append((t, None, None))
+                    break
+                curves.append((t, red["ke"] / n ** 3, lat.enstrophy()))
+                if t in error_at:
+                    lat.moments(None, uu)
+                    if dt == dtypes[0]:
+                        ref_fields[t] = uu.clone()
+                    else:
+                        r = ref_fields[t]
+                        errs[str(t)] = float(torch.linalg.vector_norm(uu - r) / torch.linalg.vector_norm(r))
+            del uu
+        out["runs"][dt] = {"glups": n ** 3 * done / t_step / 1e9, "curve_t_k_eps": curves, "vel_rel_l2_vs_first": errs}
+        torch.cuda.empty_cache()
+    return out
+
+
+def main(argv=None):  # pragma: no cover - GPU workflow entry point
+    import argparse
+    ap = argparse.ArgumentParser(description="reference workloads")
+    ap.add_argument("which", choices=["porous", "cavity", "tgv_precision"])
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--Q", type=int, default=27)
+    ap.add_argument("--t-end", type=float, default=10.0)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    if a.which == "porous":
+        res = porous(a.n or 400)
+    elif a.which == "cavity":
+        res = cavity(a.n or 256)
+    else:
+        res = tgv_precision(a.n or 512, a.Q, t_end=a.t_end)
+    text = json.dumps(res, indent=1)
+    print(text)
+    if a.out:
+        with open(a.out, "w") as fh:
+            fh.write(text)
+    return 0
+
+
+if __name__ == "__main__":  # pragma: no cover
+    sys.exit(main())

@@ -78,11 +78,18 @@ def test_f64_tgv2d_config_200_steps():
     lat.close()
 
 
+# Wall fractions below and above the 30% at which the step switches from the
+# dense sweep to the fluid-node list.
+WALL_MIX = {"dense": dict(p_solid=0.15, p_forced=0.3, p_wall=0.06),
+            "list": dict(p_solid=0.45, p_forced=0.2, p_wall=0.1)}
+
+
+@pytest.mark.parametrize("mix", ["dense", "list"])
 @pytest.mark.parametrize("Q", [19, 27])
 @pytest.mark.parametrize("closure", [lbm.CLOSURE_BGK, lbm.CLOSURE_SMAGORINSKY])
-def test_f64_tags_walls_force_ragged(Q, closure):
+def test_f64_tags_walls_force_ragged(Q, closure, mix):
     shape = (11, 13, 45)  # nx = 45: one full 32-block and a ragged tail; odd y, z
-    tags = inp.random_tags(shape, seed=9, p_solid=0.15, p_forced=0.3, p_wall=0.06, n_walls=3)
+    tags = inp.random_tags(shape, seed=9, n_walls=3, **WALL_MIX[mix])
     walls = [(0.01, 0.0, 0.0), (0.0, -0.02, 0.005), (0.003, 0.004, -0.006)]
     params = dict(tau=0.62, force=(2e-4, -1e-4, 5e-5), closure=closure, cs_smag=0.17, wall_u=walls)
     rho, u = inp.random_velocity_field(shape, seed=4, amplitude=0.04)
@@ -109,11 +116,12 @@ def test_f64_tags_walls_force_ragged(Q, closure):
     lat.close()
 
 
+@pytest.mark.parametrize("p_solid", [0.2, 0.6])
 @pytest.mark.parametrize("Q", [19, 27])
-def test_stream_only_is_bit_exact_with_bounce_back(Q):
+def test_stream_only_is_bit_exact_with_bounce_back(Q, p_solid):
     shape = (9, 10, 37)
     _, w, _ = oracle.lattice(Q)
-    tags = inp.random_tags(shape, seed=3, p_solid=0.2, p_forced=0.0, p_wall=0.0)
+    tags = inp.random_tags(shape, seed=3, p_solid=p_solid, p_forced=0.0, p_wall=0.0)
     f0 = inp.random_populations(w, shape, seed=8, amplitude=0.3)
     lat = make(shape, Q, "f64", tags, tau=1.0, closure=lbm.CLOSURE_STREAM_ONLY)
     lat.set_populations(f0)
@@ -124,6 +132,19 @@ def test_stream_only_is_bit_exact_with_bounce_back(Q):
     prob = oracle_problem(shape, Q, tags, tau=1.0, closure=oracle.STREAM_ONLY)
     g = prob.step(f_in, 3)
     assert np.array_equal(f, g)
+    lat.close()
+
+
+def test_all_solid_lattice_is_left_alone():
+    shape = (4, 5, 40)
+    _, w, _ = oracle.lattice(19)
+    f0 = inp.random_populations(w, shape, seed=4)
+    lat = make(shape, 19, "f32", np.full(shape, lbm.TAG_SOLID, np.uint8), tau=0.7)
+    lat.set_populations(f0)
+    before = lat.get_populations()
+    lat.step(3)
+    assert np.array_equal(lat.get_populations(), before)
+    assert lat.reduce()["n_fluid"] == 0
     lat.close()
 
 
@@ -250,9 +271,10 @@ HALF_SHAPES = [(10, 12, 50), (5, 7, 45), (4, 6, 150), (3, 5, 64), (6, 5, 31)]
 @pytest.mark.parametrize("shape", HALF_SHAPES)
 @pytest.mark.parametrize("kind", ["f16", "bf16"])
 @pytest.mark.parametrize("Q", [19, 27])
-def test_half_storage_one_step(kind, Q, shape):
+@pytest.mark.parametrize("mix", ["dense", "list"])
+def test_half_storage_one_step(kind, Q, shape, mix):
     _, w, _ = oracle.lattice(Q)
-    tags = inp.random_tags(shape, seed=6, p_solid=0.1, p_forced=0.3, p_wall=0.05, n_walls=2)
+    tags = inp.random_tags(shape, seed=6, n_walls=2, **WALL_MIX[mix])
     walls = [(0.02, 0.0, 0.0), (0.0, 0.01, -0.01)]
     params = dict(tau=0.7, force=(1e-3, 0.0, -5e-4), wall_u=walls)
     rho, u = inp.random_velocity_field(shape, seed=12, amplitude=0.06)
