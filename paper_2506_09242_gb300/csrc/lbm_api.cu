@@ -32,6 +32,13 @@ struct lbm_ctx {
     int *fluid_list = nullptr;    // fluid-node list (mostly-wall lattices), else NULL
     uint32_t *fluid_mask = nullptr;
     long long n_list = 0;
+    // Compact fluid-only copy of the state used while stepping with the list:
+    // populations cA/cB [Q][nfp] in list order and the neighbour index nbr.
+    void *cA = nullptr, *cB = nullptr;
+    int *nbr = nullptr;
+    long long nfp = 0;
+    bool compact_valid = false;  // cA holds the current state
+    bool dense_stale = false;    // A lacks the current state (it is in cA)
     cudaStream_t stream = nullptr;
     lbm_allocator alloc{};
     bool has_alloc = false;
@@ -111,7 +118,6 @@ Launch make_launch(lbm_ctx *ctx)
     L.general = ctx->general;
     L.closure = ctx->params.closure;
     L.mlp_image = ctx->mlp_image;
-    L.fluid_list = ctx->fluid_list;
     L.fluid_mask = ctx->fluid_mask;
     L.n_list = ctx->n_list;
     L.stream = ctx->stream;
@@ -264,9 +270,15 @@ static lbm_status build_fluid_list(lbm_ctx *ctx, bool wanted)
 {
     dev_free(ctx, ctx->fluid_list, sizeof(int) * (size_t)ctx->n_list);
     dev_free(ctx, ctx->fluid_mask, sizeof(uint32_t) * (size_t)ctx->n_list);
+    dev_free(ctx, ctx->cA, (size_t)ctx->Q * ctx->nfp * ctx->elem);
+    dev_free(ctx, ctx->cB, (size_t)ctx->Q * ctx->nfp * ctx->elem);
+    dev_free(ctx, ctx->nbr, sizeof(int) * (size_t)(ctx->Q - 1) * ctx->nfp);
     ctx->fluid_list = nullptr;
     ctx->fluid_mask = nullptr;
-    ctx->n_list = 0;
+    ctx->cA = ctx->cB = nullptr;
+    ctx->nbr = nullptr;
+    ctx->n_list = ctx->nfp = 0;
+    ctx->compact_valid = ctx->dense_stale = false;
     if (!wanted) return LBM_OK;
     const size_t rows = (size_t)ctx->g.nz * ctx->g.ny;
     Tmp count(ctx, sizeof(int) * rows);
@@ -293,8 +305,43 @@ static lbm_status build_fluid_list(lbm_ctx *ctx, bool wanted)
     CUDA_TRY(ctx, launch_fluid_scatter(ctx->Q, ctx->g, ctx->tags, (const int *)count.p, ctx->fluid_list, ctx->fluid_mask,
                                        ctx->stream),
              "fluid scatter");
+    // Compact storage and the neighbour index of every listed node.
+    ctx->nfp = (total + 255) / 256 * 256;
+    const size_t cbytes = (size_t)ctx->Q * ctx->nfp * ctx->elem;
+    ctx->cA = dev_alloc(ctx, cbytes);
+    ctx->cB = dev_alloc(ctx, cbytes);
+    ctx->nbr = (int *)dev_alloc(ctx, sizeof(int) * (size_t)(ctx->Q - 1) * ctx->nfp);
+    Tmp index(ctx, sizeof(int) * (size_t)ctx->g.sN);
+    if (!ctx->cA || !ctx->cB || !ctx->nbr || !index.p) return fail(ctx, LBM_ERR_OOM, "compact storage allocation failed");
+    CUDA_TRY(ctx, launch_build_neighbours(ctx->Q, ctx->g, ctx->tags, ctx->fluid_list, total, ctx->nfp, (int *)index.p,
+                                          ctx->nbr, ctx->stream),
+             "neighbour index");
     return sync(ctx);
 }
+
+// Brings the dense arrays up to date after steps on compact storage.
+static lbm_status ensure_dense(lbm_ctx *ctx)
+{
+    if (!ctx->dense_stale) return LBM_OK;
+    CUDA_TRY(ctx, launch_compact_copy(ctx->dtype, ctx->Q, false, ctx->cA, ctx->A, ctx->g.sN, ctx->fluid_list, ctx->n_list,
+                                      ctx->nfp, ctx->stream),
+             "compact scatter");
+    ctx->dense_stale = false;
+    return LBM_OK;
+}
+
+// The dense state was overwritten: the compact copy no longer holds it.
+static void dense_written(lbm_ctx *ctx)
+{
+    ctx->compact_valid = false;
+    ctx->dense_stale = false;
+}
+
+#define ENSURE_DENSE(ctx)                           \
+    do {                                            \
+        lbm_status es_ = ensure_dense(ctx);         \
+        if (es_ != LBM_OK) return es_;              \
+    } while (0)
 
 // ---------------------------------------------------------------------------
 // C ABI.
@@ -318,6 +365,9 @@ lbm_status lbm_destroy(lbm_ctx *ctx)
     dev_free(ctx, ctx->mlp_image, mlp_image_bytes());
     dev_free(ctx, ctx->fluid_list, sizeof(int) * (size_t)ctx->n_list);
     dev_free(ctx, ctx->fluid_mask, sizeof(uint32_t) * (size_t)ctx->n_list);
+    dev_free(ctx, ctx->cA, (size_t)ctx->Q * ctx->nfp * ctx->elem);
+    dev_free(ctx, ctx->cB, (size_t)ctx->Q * ctx->nfp * ctx->elem);
+    dev_free(ctx, ctx->nbr, sizeof(int) * (size_t)(ctx->Q - 1) * ctx->nfp);
     delete ctx;
     return LBM_OK;
 }
@@ -397,6 +447,7 @@ lbm_status lbm_set_params(lbm_ctx *ctx, const lbm_params *p)
 lbm_status lbm_set_tags(lbm_ctx *ctx, const uint8_t *tags, int on_device)
 {
     if (!ctx || !tags) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    ENSURE_DENSE(ctx);
     const size_t n = (size_t)ctx->g.N;
     Tmp user(ctx, n);
     Tmp scratch(ctx, (size_t)ctx->g.sN);
@@ -472,6 +523,7 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u
         s = sync(ctx);
     }
     ctx->steps = 0;
+    dense_written(ctx);
     return s;
 }
 
@@ -481,6 +533,30 @@ lbm_status lbm_step(lbm_ctx *ctx, int n)
     if (n < 0) return fail(ctx, LBM_ERR_ARG, "n must be >= 0");
     if (ctx->params.closure == LBM_CLOSURE_MLP && !ctx->mlp_image)
         return fail(ctx, LBM_ERR_STATE, "MLP closure selected but no weights were set (lbm_set_closure_weights)");
+    if (n == 0) return LBM_OK;
+    if (ctx->cA && ctx->params.closure != LBM_CLOSURE_MLP) {
+        // Mostly-wall lattice: step the compact fluid-only copy.
+        if (!ctx->compact_valid) {
+            CUDA_TRY(ctx, launch_compact_copy(ctx->dtype, ctx->Q, true, ctx->A, ctx->cA, ctx->g.sN, ctx->fluid_list,
+                                              ctx->n_list, ctx->nfp, ctx->stream),
+                     "compact gather");
+            ctx->compact_valid = true;
+        }
+        for (int k = 0; k < n; ++k) {
+            Launch L = make_launch(ctx);
+            CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
+                         using S = std::remove_pointer_t<decltype(tag)>;
+                         return launch_step_compact<S>(L, ctx->params, ctx->cA, ctx->cB, ctx->nbr, ctx->nfp);
+                     }),
+                     "compact collide-stream launch");
+            std::swap(ctx->cA, ctx->cB);
+            ++ctx->steps;
+        }
+        ctx->dense_stale = true;
+        return LBM_OK;
+    }
+    ENSURE_DENSE(ctx);
+    ctx->compact_valid = false;
     for (int k = 0; k < n; ++k) {
         Launch L = make_launch(ctx);
         CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
@@ -504,6 +580,7 @@ lbm_status lbm_step_count(lbm_ctx *ctx, long long *steps)
 lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *u, int on_device)
 {
     if (!ctx) return fail(ctx, LBM_ERR_ARG, "NULL context");
+    ENSURE_DENSE(ctx);
     if (!rho && !u) return LBM_OK;
     const size_t nb = sizeof(double) * (size_t)ctx->g.N;
     Launch L = make_launch(ctx);
@@ -530,6 +607,7 @@ lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *u, int on_device)
 lbm_status lbm_reduce(lbm_ctx *ctx, lbm_reduction *out)
 {
     if (!ctx || !out) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    ENSURE_DENSE(ctx);
     const long long total = (long long)ctx->g.nz * ctx->g.ny * ctx->g.px;
     long long nb = (total + kRedThreads - 1) / kRedThreads;
     if (nb > kRedBlocks) nb = kRedBlocks;
@@ -566,6 +644,7 @@ lbm_status lbm_sync(lbm_ctx *ctx, int timeout_ms)
 lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int on_device)
 {
     if (!ctx || !f) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    ENSURE_DENSE(ctx);
     const size_t nb = sizeof(double) * (size_t)ctx->g.N;
     Tmp plane(ctx, on_device ? 0 : nb);
     if (!on_device && !plane.p) return fail(ctx, LBM_ERR_OOM, "staging allocation failed");
@@ -588,6 +667,7 @@ lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int on_device)
 lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device)
 {
     if (!ctx || !f) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    dense_written(ctx);
     const size_t nb = sizeof(double) * (size_t)ctx->g.N;
     Tmp plane(ctx, on_device ? 0 : nb);
     if (!on_device && !plane.p) return fail(ctx, LBM_ERR_OOM, "staging allocation failed");
@@ -661,6 +741,7 @@ lbm_status lbm_geometry_spheres(lbm_ctx *ctx, const int32_t *centres, const doub
 lbm_status lbm_enstrophy(lbm_ctx *ctx, double *out)
 {
     if (!ctx || !out) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    ENSURE_DENSE(ctx);
     const long long N = ctx->g.N;
     Tmp u(ctx, 3 * sizeof(double) * (size_t)N);
     if (!u.p) return fail(ctx, LBM_ERR_OOM, "velocity staging allocation failed");

@@ -125,14 +125,16 @@ struct Launch {
     bool general;             // tags present (not all FLUID)
     int closure;
     const void *mlp_image;    // device packed closure network (MlpSmem, closure 2)
-    const int *fluid_list;    // padded offsets of the fluid nodes, or NULL (dense sweep)
-    const uint32_t *fluid_mask;
-    long long n_list;
+    const uint32_t *fluid_mask;  // per listed fluid node: kListForced (compact step)
+    long long n_list;            // number of listed fluid nodes
     cudaStream_t stream;
 };
 
 // Per-storage-type launchers (one translation unit per type).
 template <typename S> cudaError_t launch_step(const Launch &L, const lbm_params &p);
+template <typename S>
+cudaError_t launch_step_compact(const Launch &L, const lbm_params &p, const void *Ac, void *Bc, const int *nbr,
+                                long long nfp);
 template <typename S>
 cudaError_t launch_reduce(const Launch &L, const lbm_params &p, double *partials, int nblocks, double *out);
 template <typename S>
@@ -151,6 +153,10 @@ cudaError_t launch_gather_tags(const Grid &g, const uint8_t *tags, uint8_t *out,
 cudaError_t launch_fluid_count(const Grid &g, const uint8_t *tags, int *count, cudaStream_t s);
 cudaError_t launch_fluid_scatter(int Q, const Grid &g, const uint8_t *tags, const int *start, int *list,
                                  uint32_t *mask, cudaStream_t s);
+cudaError_t launch_build_neighbours(int Q, const Grid &g, const uint8_t *tags, const int *list, long long n,
+                                    long long nfp, int *index, int *nbr, cudaStream_t s);
+cudaError_t launch_compact_copy(lbm_dtype dtype, int Q, bool to_compact, const void *src, void *dst, long long sN,
+                                const int *list, long long n, long long nfp, cudaStream_t s);
 
 // Porous-medium generator and enstrophy diagnostic (lbm_diag.cu).
 cudaError_t launch_sphere_cover(int nx, int ny, int nz, const int *centres, const double *radii, int n,

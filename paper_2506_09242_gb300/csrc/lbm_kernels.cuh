@@ -236,14 +236,8 @@ __global__ void __launch_bounds__(kStepThreads)
     for (int i = 0; i < Q; ++i) St::st(B + (long long)i * g.sN + nb.self, h[i]);
 }
 
-// ---------------------------------------------------------------------------
-// The step over a list of fluid nodes (lattices that are mostly wall, e.g.
-// porous media): one thread per listed node, solid nodes are never visited.
-// Each node's link mask says which pull sources are walls, so a direction
-// costs one load either way (the neighbour's population, or the node's own
-// opposite population for bounce-back); tags are read only for links to a
-// moving wall.
-// ---------------------------------------------------------------------------
+// Ladd's moving-wall term 6 w_i rho_wall (c_i . u_wall) of the wall whose tag
+// is ts, selected without dynamic indexing of the parameter block.
 template <int Q, typename T>
 __device__ __forceinline__ T wall_term(int i, unsigned ts, const KParams<T> &p)
 {
@@ -258,37 +252,38 @@ __device__ __forceinline__ T wall_term(int i, unsigned ts, const KParams<T> &p)
     return wgt<T>(Q, i) * (T(cvel(i, 0)) * ux + T(cvel(i, 1)) * uy + T(cvel(i, 2)) * uz);
 }
 
+// ---------------------------------------------------------------------------
+// The step on compact fluid-only storage (lattices that are mostly wall, e.g.
+// porous media): one thread per fluid node, populations A[Q][nfp] in the
+// order of the fluid-node list, and the neighbour index nbr[i-1][k] of each
+// pull source (its list position, -1 for SOLID, -2 - w for moving wall w), so
+// every load and store touches fluid data only and a bounced link costs the
+// same single load as a streamed one.  (The learned closure needs whole warps
+// of consecutive nodes and keeps the dense sweep.)
+// ---------------------------------------------------------------------------
 template <int Q, typename S, int CLOSURE>
 __global__ void __launch_bounds__(kStepThreads)
-    k_collide_stream_list(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ tags, Grid g,
-                          KParams<typename Store<S>::T> p, const int *__restrict__ list,
-                          const uint32_t *__restrict__ mask, long long n)
+    k_collide_stream_compact(const S *__restrict__ A, S *__restrict__ B, const int *__restrict__ nbr,
+                             const uint32_t *__restrict__ mask, long long n, long long nfp,
+                             KParams<typename Store<S>::T> p)
 {
     using T = typename Store<S>::T;
     using St = Store<S>;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= n) return;
-    const int off = __ldg(list + t);
-    const uint32_t m = __ldg(mask + t);
-    const int r = off / g.px;
-    Nbr nb;
-    nb.init(g, off - r * g.px, r % g.ny, r / g.ny);
     T h[Q];
-    h[0] = St::ld(A + nb.self);
+    h[0] = St::ld(A + t);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        const bool bb = (m >> i) & 1u;
-        const long long a = bb ? (long long)opp(i) * g.sN + nb.self : (long long)i * g.sN + nb.src(i);
+        const int s = __ldg(nbr + (long long)(i - 1) * nfp + t);
+        const long long a = s >= 0 ? (long long)i * nfp + s : (long long)opp(i) * nfp + t;
         T v = St::ld(A + a);
-        if (bb && (m & kListAnyWall)) {
-            const unsigned ts = tags[nb.src(i)] & kTagMask;
-            if (ts >= LBM_TAG_WALL0) v += wall_term<Q, T>(i, ts, p);
-        }
+        if (s < -1) v += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - s), p);
         h[i] = v;
     }
-    collide_node<Q, T, CLOSURE>(h, (m & kListForced) != 0u, p);
+    collide_node<Q, T, CLOSURE>(h, (__ldg(mask + t) & kListForced) != 0u, p);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) St::st(B + (long long)i * g.sN + nb.self, h[i]);
+    for (int i = 0; i < Q; ++i) St::st(B + (long long)i * nfp + t, h[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -799,39 +794,11 @@ cudaError_t step_closure(const Launch &L, const KParams<typename Store<S>::T> &k
     return cudaGetLastError();
 }
 
-template <int Q, typename S>
-cudaError_t step_list(const Launch &L, const KParams<typename Store<S>::T> &kp)
-{
-    const S *A = (const S *)L.A;
-    S *B = (S *)L.B;
-    const unsigned blocks = (unsigned)((L.n_list + kStepThreads - 1) / kStepThreads);
-    if (blocks == 0) return cudaSuccess;
-    switch (L.closure) {
-    case LBM_CLOSURE_BGK:
-        k_collide_stream_list<Q, S, LBM_CLOSURE_BGK>
-            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, L.tags, L.g, kp, L.fluid_list, L.fluid_mask, L.n_list);
-        break;
-    case LBM_CLOSURE_SMAGORINSKY:
-        k_collide_stream_list<Q, S, LBM_CLOSURE_SMAGORINSKY>
-            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, L.tags, L.g, kp, L.fluid_list, L.fluid_mask, L.n_list);
-        break;
-    case LBM_CLOSURE_STREAM_ONLY:
-        k_collide_stream_list<Q, S, LBM_CLOSURE_STREAM_ONLY>
-            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, L.tags, L.g, kp, L.fluid_list, L.fluid_mask, L.n_list);
-        break;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
 template <int Q, typename S> cudaError_t step_q(const Launch &L, const lbm_params &p)
 {
     dim3 grid, block;
     node_launch_shape(L.g, grid, block);
     const auto kp = make_kparams<typename Store<S>::T>(Q, p);
-    // Mostly-wall lattices walk the fluid-node list (the learned closure
-    // needs whole warps of consecutive nodes and keeps the dense sweep).
-    if (L.fluid_list && L.closure != LBM_CLOSURE_MLP) return step_list<Q, S>(L, kp);
     return L.general ? step_closure<Q, S, true>(L, kp, grid, block) : step_closure<Q, S, false>(L, kp, grid, block);
 }
 
@@ -861,7 +828,41 @@ template <int Q, typename S> cudaError_t moments_q(const Launch &L, const lbm_pa
     return cudaGetLastError();
 }
 
+template <int Q, typename S>
+cudaError_t step_compact_q(const Launch &L, const lbm_params &p, const void *Ac, void *Bc, const int *nbr,
+                           long long nfp)
+{
+    const auto kp = make_kparams<typename Store<S>::T>(Q, p);
+    const unsigned blocks = (unsigned)((L.n_list + kStepThreads - 1) / kStepThreads);
+    if (blocks == 0) return cudaSuccess;
+    const S *A = (const S *)Ac;
+    S *B = (S *)Bc;
+    switch (L.closure) {
+    case LBM_CLOSURE_BGK:
+        k_collide_stream_compact<Q, S, LBM_CLOSURE_BGK>
+            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
+        break;
+    case LBM_CLOSURE_SMAGORINSKY:
+        k_collide_stream_compact<Q, S, LBM_CLOSURE_SMAGORINSKY>
+            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
+        break;
+    case LBM_CLOSURE_STREAM_ONLY:
+        k_collide_stream_compact<Q, S, LBM_CLOSURE_STREAM_ONLY>
+            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 #define LBM_DEFINE_LAUNCHERS(S)                                                                              \
+    template <>                                                                                              \
+    cudaError_t launch_step_compact<S>(const Launch &L, const lbm_params &p, const void *Ac, void *Bc,       \
+                                       const int *nbr, long long nfp)                                        \
+    {                                                                                                        \
+        return L.Q == 19 ? step_compact_q<19, S>(L, p, Ac, Bc, nbr, nfp)                                    \
+                         : step_compact_q<27, S>(L, p, Ac, Bc, nbr, nfp);                                   \
+    }                                                                                                        \
     template <> cudaError_t launch_step<S>(const Launch &L, const lbm_params &p)                             \
     {                                                                                                        \
         return L.Q == 19 ? step_q<19, S>(L, p) : step_q<27, S>(L, p);                                       \

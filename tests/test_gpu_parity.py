@@ -135,6 +135,43 @@ def test_stream_only_is_bit_exact_with_bounce_back(Q, p_solid):
     lat.close()
 
 
+def test_compact_and_dense_paths_hand_over_the_state():
+    """Mostly-wall tags step the compact fluid-only copy; accessors and a tag
+    change in mid-run must see the state of every step taken so far."""
+    shape = (9, 11, 40)
+    Q = 19
+    tags_a = inp.random_tags(shape, seed=31, **WALL_MIX["list"])
+    tags_b = inp.random_tags(shape, seed=32, **WALL_MIX["dense"])
+    tags_b[tags_a >= oracle.SOLID] = tags_a[tags_a >= oracle.SOLID]  # keep the walls, open some pores
+    walls = [(0.01, 0.0, 0.0), (0.0, -0.01, 0.0), (0.0, 0.0, 0.02)]
+    params = dict(tau=0.65, force=(1e-4, 0.0, 0.0), wall_u=walls)
+    rho, u = inp.random_velocity_field(shape, seed=33, amplitude=0.04)
+    lat = make(shape, Q, "f64", tags_a, **params)
+    lat.init_equilibrium(rho, u)
+    pa = oracle_problem(shape, Q, tags_a, **params)
+    pb = oracle_problem(shape, Q, tags_b, **params)
+    g = pa.init_equilibrium(rho, u)
+    lat.step(5)
+    g = pa.step(g, 5)
+    assert lat.reduce()["mass"] == pytest.approx(pa.reduce(g)["mass"], rel=1e-13)
+    lat.step(4)
+    g = pa.step(g, 4)
+    assert max_rel(lat.get_populations(), g) <= 1e-12
+    lat.step(3)
+    g = pa.step(g, 3)
+    lat.set_tags(tags_b)  # mostly fluid now: dense sweep from here
+    lat.step(6)
+    g = pb.step(g, 6)
+    assert max_rel(lat.get_populations(), g) <= 1e-12
+    lat.set_tags(tags_a)  # and back to the compact copy
+    lat.step(2)
+    g = pa.step(g, 2)
+    _, ug = lat.moments()
+    _, ur = pa.moments(g)
+    assert np.max(np.abs(ug - ur)) <= 1e-13
+    lat.close()
+
+
 def test_all_solid_lattice_is_left_alone():
     shape = (4, 5, 40)
     _, w, _ = oracle.lattice(19)
