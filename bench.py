@@ -260,6 +260,21 @@ def time_e2e(lat, fields, steps: int, inner: int):
     return ms, h2d, d2h
 
 
+def replica_throughput(local_ms: float, local_updates: int, dist=None, device: str = "cpu"):
+    """Whole-job throughput of independent replicas (one lattice per rank, no
+    exchange): node updates summed over ranks divided by the slowest rank's
+    time.  Returns (GLUPS, max ms)."""
+    if dist is None:
+        return local_updates / (local_ms * 1e-3) / 1e9, local_ms
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    ms = float(t.item())
+    return float(u.item()) / (ms * 1e-3) / 1e9, ms
+
+
 def oracle_glups(n: int = 64, target_s: float = 12.0):
     """FP64 CPU oracle on the host: periodic 3D TGV, D3Q19, n^3, single thread.
     Returns (GLUPS, seconds, steps, sample description)."""
@@ -362,12 +377,7 @@ def run_ours(args):
     sampler.start()
     total_ms, kernel_ms, reds = time_lattice(lat, args.steps, args.warmup, args.inner, sync_all)
     clocks = sampler.stop()
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    updates = cells * args.inner * args.steps * world
-    glups = updates / (total_ms * 1e-3) / 1e9
+    glups, total_ms = replica_throughput(total_ms, cells * args.inner * args.steps, dist, "cuda")
 
     # roofline of the dominant kernel (collide-stream), timed on its stream
     alg_bytes = 2 * Q * SIZE[args.dtype] * cells
@@ -375,9 +385,9 @@ def run_ours(args):
     peak, peak_kind = measured_peak_hbm()
     traffic = recorded_traffic(desc["workload"])
 
-    e2e_ms, h2d, d2h = time_e2e(lat, fields, max(2, args.steps // 2), args.inner)
     e2e_steps = max(2, args.steps // 2)
-    e2e_glups = cells * args.inner * e2e_steps * world / (e2e_ms * 1e-3) / 1e9
+    e2e_ms, h2d, d2h = time_e2e(lat, fields, e2e_steps, args.inner)
+    e2e_glups, _ = replica_throughput(e2e_ms, cells * args.inner * e2e_steps, dist, "cuda")
     lat.close()
     del lat
     torch.cuda.empty_cache()
