@@ -73,7 +73,8 @@ typedef enum {
     LBM_CLOSURE_BGK = 0,         /* BGK with the 2nd-order weighted equilibrium (Sec. 3.1) */
     LBM_CLOSURE_SMAGORINSKY = 1, /* BGK with a Smagorinsky eddy viscosity (Sec. 2.3.2)     */
     LBM_CLOSURE_MLP = 2,         /* BGK with a learned per-cell relaxation-time correction */
-    LBM_CLOSURE_STREAM_ONLY = 3  /* no collision: pure streaming, for verification        */
+    LBM_CLOSURE_STREAM_ONLY = 3, /* no collision: pure streaming, for verification        */
+    LBM_CLOSURE_TRT = 4          /* two relaxation times (Sec. 3.3's porous-rock model)    */
 } lbm_closure;
 
 /* Optional device allocator.  alloc returns device memory of at least
@@ -92,7 +93,11 @@ typedef struct {
  *  cs_smag  Smagorinsky constant (closure 1).
  *  wall_u   velocity of moving wall k, used by Ladd's bounce-back
  *           f_i(x) = f*_opp(i)(x) + 6 w_i rho_wall (c_i . wall_u[k]).
- *  rho_wall density in Ladd's wall term (the reference density, 1). */
+ *  rho_wall density in Ladd's wall term (the reference density, 1).
+ *  trt_magic TRT's Lambda = (tau - 1/2)(tau_minus - 1/2) > 0, which sets the
+ *           relaxation time tau_minus of the part of the populations that is
+ *           odd under i -> opp(i); tau relaxes the even part.  Lambda = 3/16
+ *           puts halfway bounce-back walls exactly halfway at any tau. */
 typedef struct {
     double tau;
     double force[3];
@@ -100,6 +105,7 @@ typedef struct {
     double cs_smag;
     double wall_u[LBM_NWALLS][3];
     double rho_wall;
+    double trt_magic;
 } lbm_params;
 
 /* Sums over fluid nodes (tags FLUID and FORCED), accumulated in FP64 from
@@ -131,7 +137,7 @@ lbm_status lbm_create(int nx, int ny, int nz, lbm_lattice lattice, lbm_dtype dty
 lbm_status lbm_destroy(lbm_ctx *ctx);
 
 /* Sets the model parameters.  Errors: ARG (tau <= 1/2 or not finite,
- * unknown closure, cs_smag < 0). */
+ * unknown closure, cs_smag < 0, trt_magic <= 0 with LBM_CLOSURE_TRT). */
 lbm_status lbm_set_params(lbm_ctx *ctx, const lbm_params *p);
 
 /* Sets the tag of every node (N bytes, values below LBM_NTAGS), derives the
@@ -159,6 +165,15 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u
  * other array.  Asynchronous.  Errors: ARG (n < 0), STATE (MLP closure
  * without weights), CUDA (launch failure). */
 lbm_status lbm_step(lbm_ctx *ctx, int n);
+
+/* Enables (default) or disables replaying pairs of steps as CUDA graphs in
+ * lbm_step.  With graphs, lbm_step(n >= 4) captures a two-step graph once
+ * per kernel path and array orientation (again after lbm_set_params or
+ * lbm_set_tags) and replays it on a private stream ordered after and before
+ * the context's stream, so results and stream semantics are the same as
+ * with one launch per step.  A capture the driver refuses turns graphs off
+ * for the context. */
+lbm_status lbm_use_graphs(lbm_ctx *ctx, int enable);
 
 /* Number of steps taken since the last initialisation. */
 lbm_status lbm_step_count(lbm_ctx *ctx, long long *steps);

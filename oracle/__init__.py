@@ -27,7 +27,7 @@ _LIB = _HERE / "_build" / "liblbm_oracle.so"
 # scheme of Sec. 2.3.2; the CUDA library declares the same values itself).
 FLUID, FORCED, SOLID, WALL0 = 0, 1, 2, 3
 NWALLS = 8
-BGK, SMAGORINSKY, MLP, STREAM_ONLY = 0, 1, 2, 3
+BGK, SMAGORINSKY, MLP, STREAM_ONLY, TRT = 0, 1, 2, 3, 4
 F64, F32, F16, BF16 = 0, 1, 2, 3
 MLP_NPARAM = 32 * 7 + 32 + 32 * 32 + 32 + 32 + 1
 
@@ -55,6 +55,7 @@ class Params(ctypes.Structure):
         ("mlp_params", ctypes.POINTER(ctypes.c_double)),
         ("mlp_norm", ctypes.POINTER(ctypes.c_double)),
         ("mlp_bf16", ctypes.c_int),
+        ("trt_magic", ctypes.c_double),
     ]
 
 
@@ -157,7 +158,7 @@ class Problem:
     def __init__(self, Q: int, nx: int, ny: int, nz: int, tags=None, *, tau: float,
                  force=(0.0, 0.0, 0.0), closure: int = BGK, cs_smag: float = 0.0,
                  wall_u=None, rho_wall: float = 1.0, mlp_params=None, mlp_norm=None,
-                 mlp_bf16: bool = False):
+                 mlp_bf16: bool = False, trt_magic: float = 3.0 / 16.0):
         self.Q, self.nx, self.ny, self.nz = Q, nx, ny, nz
         self.tags = None if tags is None else np.ascontiguousarray(tags, dtype=np.uint8).reshape(nz, ny, nx)
         self.p = Params()
@@ -177,6 +178,7 @@ class Problem:
             self.p.mlp_params = self._mlp.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             self.p.mlp_norm = self._norm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         self.p.mlp_bf16 = int(mlp_bf16)
+        self.p.trt_magic = trt_magic
 
     @property
     def shape(self):

@@ -23,6 +23,8 @@
  *   - Cell behaviour chosen by an integer tag per node (Sec. 2.3.2).
  *   - Body force by Guo, Zheng & Shi (2002) on tagged cells (no text in the
  *     paper; the paper drives its porous flow by boundary conditions).
+ *   - TRT collision (the paper's model for the porous rock of Sec. 3.3), two
+ *     relaxation rates for the even and odd parts under i -> opp(i).
  *   - Smagorinsky eddy viscosity (cited in Sec. 2.3.2 as a per-node model
  *     with its own parameter) written in closed form for tau_eff.
  *   - A per-cell MLP relaxation-time closure (no counterpart in the paper).
@@ -65,7 +67,7 @@ enum {
 static int is_wall_or_solid(unsigned char t) { return t >= ORC_SOLID && t < ORC_WALL0 + ORC_NWALLS; }
 
 /* Closures. */
-enum { ORC_BGK = 0, ORC_SMAGORINSKY = 1, ORC_MLP = 2, ORC_STREAM_ONLY = 3 };
+enum { ORC_BGK = 0, ORC_SMAGORINSKY = 1, ORC_MLP = 2, ORC_STREAM_ONLY = 3, ORC_TRT = 4 };
 
 /* Storage emulation. */
 enum { ORC_F64 = 0, ORC_F32 = 1, ORC_F16 = 2, ORC_BF16 = 3 };
@@ -85,6 +87,7 @@ typedef struct {
     const double *mlp_params;        /* ORC_MLP_NPARAM values (closure 2)   */
     const double *mlp_norm;          /* mean[7], std[7], out_scale, unused  */
     int mlp_bf16;                    /* 1: round MLP operands to bf16       */
+    double trt_magic;                /* TRT: Lambda = (tau+ - 1/2)(tau- - 1/2) */
 } orc_params;
 
 typedef struct {
@@ -303,6 +306,21 @@ static void collide(int Q, const orc_params *p, int forced, const double *f, dou
         }
     }
     double omega = 1.0 / tau;
+    if (p->closure == ORC_TRT) {
+        /* Two relaxation times (Ginzburg): the parts of f, f_eq and F that are
+         * even and odd under i -> opp(i) relax with omega+ = 1/tau and
+         * omega- from the magic parameter Lambda = (1/omega+ - 1/2)(1/omega- - 1/2). */
+        const double wp = omega;
+        const double wm = 1.0 / (0.5 + p->trt_magic / (tau - 0.5));
+        for (int i = 0; i < Q; ++i) {
+            const int o = opposite_of(Q, i);
+            const double fp = 0.5 * (f[i] + f[o]), fm = 0.5 * (f[i] - f[o]);
+            const double ep = 0.5 * (feq[i] + feq[o]), em = 0.5 * (feq[i] - feq[o]);
+            const double Fp = 0.5 * (F[i] + F[o]), Fm = 0.5 * (F[i] - F[o]);
+            fout[i] = f[i] - wp * (fp - ep) - wm * (fm - em) + (1.0 - 0.5 * wp) * Fp + (1.0 - 0.5 * wm) * Fm;
+        }
+        return;
+    }
     for (int i = 0; i < Q; ++i) fout[i] = f[i] - omega * (f[i] - feq[i]) + (1.0 - 0.5 * omega) * F[i];
 }
 
@@ -320,6 +338,7 @@ int orc_step(int Q, int nx, int ny, int nz, const unsigned char *tags, const orc
 {
     if (Q != 19 && Q != 27) return -1;
     if (nx < 1 || ny < 1 || nz < 1 || !(p->tau > 0.5)) return -1;
+    if (p->closure == ORC_TRT && !(p->trt_magic > 0.0)) return -1;
     const long long N = (long long)nx * ny * nz;
     for (long long z = 0; z < nz; ++z)
         for (long long y = 0; y < ny; ++y)

@@ -39,6 +39,20 @@ struct lbm_ctx {
     long long nfp = 0;
     bool compact_valid = false;  // cA holds the current state
     bool dense_stale = false;    // A lacks the current state (it is in cA)
+    // CUDA graphs of two steps (X -> Y, Y -> X), replayed on a private stream
+    // ordered after / before the caller's stream by events.  One graph per
+    // kernel path (dense, compact) and array orientation; any change of
+    // parameters or tags bumps `version` and invalidates them.
+    bool use_graphs = true;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        const void *first = nullptr;  // the array the graph reads first
+        int path = -1;                // 0 dense, 1 compact
+        unsigned long long version = 0;
+    } graphs[4];
+    unsigned long long version = 1;
     cudaStream_t stream = nullptr;
     lbm_allocator alloc{};
     bool has_alloc = false;
@@ -158,7 +172,9 @@ lbm_status sync(lbm_ctx *ctx) { return wait_stream(ctx, -1); }
 bool valid_params(const lbm_params *p, std::string &why)
 {
     if (!(p->tau > 0.5) || !isfinite(p->tau)) return why = "tau must be finite and > 1/2", false;
-    if (p->closure < LBM_CLOSURE_BGK || p->closure > LBM_CLOSURE_STREAM_ONLY) return why = "unknown closure", false;
+    if (p->closure < LBM_CLOSURE_BGK || p->closure > LBM_CLOSURE_TRT) return why = "unknown closure", false;
+    if (p->closure == LBM_CLOSURE_TRT && !(p->trt_magic > 0.0 && isfinite(p->trt_magic)))
+        return why = "TRT needs a finite trt_magic > 0", false;
     if (!(p->cs_smag >= 0.0) || !isfinite(p->cs_smag)) return why = "cs_smag must be >= 0", false;
     for (int a = 0; a < 3; ++a)
         if (!isfinite(p->force[a])) return why = "force must be finite", false;
@@ -355,6 +371,15 @@ lbm_status lbm_destroy(lbm_ctx *ctx)
     if (!ctx) return LBM_OK;
     cudaStreamSynchronize(ctx->stream);
     cudaGetLastError();
+    for (auto &gr : ctx->graphs)
+        if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    if (ctx->gstream) {
+        cudaStreamSynchronize(ctx->gstream);
+        cudaStreamDestroy(ctx->gstream);
+    }
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+    cudaGetLastError();
     dev_free(ctx, ctx->A, ctx->pop_bytes);
     dev_free(ctx, ctx->B, ctx->pop_bytes);
     dev_free(ctx, ctx->tags, (size_t)ctx->g.sN);
@@ -410,6 +435,7 @@ lbm_status lbm_create(int nx, int ny, int nz, lbm_lattice lattice, lbm_dtype dty
     ctx->params.tau = 1.0;
     ctx->params.closure = LBM_CLOSURE_BGK;
     ctx->params.rho_wall = 1.0;
+    ctx->params.trt_magic = 3.0 / 16.0;
 
     ctx->A = dev_alloc(ctx, ctx->pop_bytes);
     ctx->B = dev_alloc(ctx, ctx->pop_bytes);
@@ -441,6 +467,7 @@ lbm_status lbm_set_params(lbm_ctx *ctx, const lbm_params *p)
     std::string why;
     if (!valid_params(p, why)) return fail(ctx, LBM_ERR_ARG, "%s", why.c_str());
     ctx->params = *p;
+    ++ctx->version;
     return LBM_OK;
 }
 
@@ -474,6 +501,7 @@ lbm_status lbm_set_tags(lbm_ctx *ctx, const uint8_t *tags, int on_device)
         if (is_wall_tag((unsigned)k)) walls += (long long)c[k];
     }
     ctx->general = general;
+    ++ctx->version;
     s = build_fluid_list(ctx, walls > kListWallFraction * (double)ctx->g.N);
     if (s != LBM_OK) return s;
     return sync(ctx);
@@ -527,6 +555,103 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u
     return s;
 }
 
+// One collide-and-stream launch of the current path from X to Y on stream st.
+static cudaError_t launch_one(lbm_ctx *ctx, bool compact, const void *X, void *Y, cudaStream_t st)
+{
+    Launch L = make_launch(ctx);
+    L.stream = st;
+    if (compact)
+        return by_dtype(ctx->dtype, [&](auto *tag) {
+            using S = std::remove_pointer_t<decltype(tag)>;
+            return launch_step_compact<S>(L, ctx->params, X, Y, ctx->nbr, ctx->nfp);
+        });
+    L.A = X;
+    L.B = Y;
+    return by_dtype(ctx->dtype, [&](auto *tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        return launch_step<S>(L, ctx->params);
+    });
+}
+
+// The two-step graph for the current path and orientation, captured on first
+// use.  Returns nullptr when graphs cannot be used (capture refused).
+static cudaGraphExec_t two_step_graph(lbm_ctx *ctx, bool compact, const void *X, void *Y)
+{
+    const int path = compact ? 1 : 0;
+    lbm_ctx::Graph *slot = nullptr;
+    for (auto &gr : ctx->graphs)
+        if (gr.exec && gr.path == path && gr.first == X && gr.version == ctx->version) return gr.exec;
+    for (auto &gr : ctx->graphs)
+        if (!gr.exec || gr.version != ctx->version) {
+            slot = &gr;
+            break;
+        }
+    if (!slot) slot = &ctx->graphs[0];
+    if (slot->exec) {
+        cudaGraphExecDestroy(slot->exec);
+        slot->exec = nullptr;
+    }
+    if (!ctx->gstream) {
+        if (cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->use_graphs = false;
+            return nullptr;
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->use_graphs = false;
+        return nullptr;
+    }
+    const cudaError_t e1 = launch_one(ctx, compact, X, Y, ctx->gstream);
+    const cudaError_t e2 = launch_one(ctx, compact, Y, (void *)X, ctx->gstream);
+    const cudaError_t e3 = cudaStreamEndCapture(ctx->gstream, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && graph &&
+        cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+        slot->exec = exec;
+        slot->first = X;
+        slot->path = path;
+        slot->version = ctx->version;
+    } else {
+        exec = nullptr;
+        ctx->use_graphs = false;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return exec;
+}
+
+// n steps on the current path: pairs of steps as graph replays (when n is
+// large enough and graphs are enabled), the remainder as plain launches.
+static lbm_status run_steps(lbm_ctx *ctx, int n, bool compact)
+{
+    void **X = compact ? &ctx->cA : &ctx->A;
+    void **Y = compact ? &ctx->cB : &ctx->B;
+    int pairs = (ctx->use_graphs && n >= 4) ? n / 2 : 0;
+    if (pairs) {
+        cudaGraphExec_t exec = two_step_graph(ctx, compact, *X, *Y);
+        if (exec) {
+            CUDA_TRY(ctx, cudaEventRecord(ctx->ev_in, ctx->stream), "graph order");
+            CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev_in, 0), "graph order");
+            for (int r = 0; r < pairs; ++r) CUDA_TRY(ctx, cudaGraphLaunch(exec, ctx->gstream), "graph launch");
+            CUDA_TRY(ctx, cudaEventRecord(ctx->ev_out, ctx->gstream), "graph order");
+            CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_out, 0), "graph order");
+            ctx->steps += 2LL * pairs;
+            n -= 2 * pairs;  // an even number of steps leaves X and Y in place
+        }
+    }
+    for (int k = 0; k < n; ++k) {
+        CUDA_TRY(ctx, launch_one(ctx, compact, *X, *Y, ctx->stream), "collide-stream launch");
+        std::swap(*X, *Y);
+        ++ctx->steps;
+    }
+    return LBM_OK;
+}
+
 lbm_status lbm_step(lbm_ctx *ctx, int n)
 {
     if (!ctx) return fail(ctx, LBM_ERR_ARG, "NULL context");
@@ -542,31 +667,18 @@ lbm_status lbm_step(lbm_ctx *ctx, int n)
                      "compact gather");
             ctx->compact_valid = true;
         }
-        for (int k = 0; k < n; ++k) {
-            Launch L = make_launch(ctx);
-            CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
-                         using S = std::remove_pointer_t<decltype(tag)>;
-                         return launch_step_compact<S>(L, ctx->params, ctx->cA, ctx->cB, ctx->nbr, ctx->nfp);
-                     }),
-                     "compact collide-stream launch");
-            std::swap(ctx->cA, ctx->cB);
-            ++ctx->steps;
-        }
         ctx->dense_stale = true;
-        return LBM_OK;
+        return run_steps(ctx, n, true);
     }
     ENSURE_DENSE(ctx);
     ctx->compact_valid = false;
-    for (int k = 0; k < n; ++k) {
-        Launch L = make_launch(ctx);
-        CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
-                     using S = std::remove_pointer_t<decltype(tag)>;
-                     return launch_step<S>(L, ctx->params);
-                 }),
-                 "collide-stream launch");
-        std::swap(ctx->A, ctx->B);
-        ++ctx->steps;
-    }
+    return run_steps(ctx, n, false);
+}
+
+lbm_status lbm_use_graphs(lbm_ctx *ctx, int enable)
+{
+    if (!ctx) return fail(ctx, LBM_ERR_ARG, "NULL context");
+    ctx->use_graphs = enable != 0;
     return LBM_OK;
 }
 

@@ -99,6 +99,7 @@ struct Grid {
 // Parameters in the compute type.
 template <typename T> struct KParams {
     T omega;                      // 1 / tau
+    T omega_minus;                // TRT: 1 / tau_minus
     T tau;                        // tau
     T force[3];                   // g
     T smag18;                     // 18 Cs^2

@@ -21,6 +21,7 @@ template <typename T> inline KParams<T> make_kparams(int Q, const lbm_params &p)
     KParams<T> k;
     k.tau = (T)p.tau;
     k.omega = (T)(1.0 / p.tau);
+    k.omega_minus = p.trt_magic > 0.0 ? (T)(1.0 / (0.5 + p.trt_magic / (p.tau - 0.5))) : k.omega;
     for (int a = 0; a < 3; ++a) k.force[a] = (T)p.force[a];
     k.smag18 = (T)(18.0 * p.cs_smag * p.cs_smag);
     for (int w = 0; w < LBM_NWALLS; ++w)
@@ -182,11 +183,52 @@ __device__ __forceinline__ void relax(T (&h)[Q], const Macro<T> &m, T omega, boo
     }
 }
 
+// TRT (Ginzburg): the parts of h, h_eq and the Guo source that are even and
+// odd under i -> opp(i) relax with omega and omega_minus.  With
+// h_eq_i = S + A and h_eq_opp(i) = S - A, S = w (drho + rho (4.5 (c.u)^2 -
+// 1.5 u^2)), A = 3 w rho (c.u), and the source split the same way.
+template <int Q, typename T>
+__device__ __forceinline__ void relax_trt(T (&h)[Q], const Macro<T> &m, T wp, T wm, bool forced)
+{
+    const T usq15 = T(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+    const T cfp = T(1) - T(0.5) * wp, cfm = T(1) - T(0.5) * wm;
+    const T uG = m.ux * m.Gx + m.uy * m.Gy + m.uz * m.Gz;
+    {
+        const T w0 = wgt<T>(Q, 0);
+        T h0 = h[0] - wp * (h[0] - w0 * (m.drho - m.rho * usq15));
+        if (forced) h0 += cfp * w0 * (T(-3) * uG);
+        h[0] = h0;
+    }
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
+        const T cu = T(cx) * m.ux + T(cy) * m.uy + T(cz) * m.uz;
+        const T w = wgt<T>(Q, i);
+        const T S = w * (m.drho + m.rho * (T(4.5) * cu * cu - usq15));
+        const T A = T(3) * w * m.rho * cu;
+        const T dp = wp * (T(0.5) * (h[i] + h[i + 1]) - S);
+        const T dm = wm * (T(0.5) * (h[i] - h[i + 1]) - A);
+        T hi = h[i] - dp - dm, ho = h[i + 1] - dp + dm;
+        if (forced) {
+            const T cG = T(cx) * m.Gx + T(cy) * m.Gy + T(cz) * m.Gz;
+            const T Fs = w * (T(9) * cu * cG - T(3) * uG), Fa = T(3) * w * cG;
+            hi += cfp * Fs + cfm * Fa;
+            ho += cfp * Fs - cfm * Fa;
+        }
+        h[i] = hi;
+        h[i + 1] = ho;
+    }
+}
+
 template <int Q, typename T, int CLOSURE>
 __device__ __forceinline__ void collide_node(T (&h)[Q], bool forced, const KParams<T> &p)
 {
     if (CLOSURE == LBM_CLOSURE_STREAM_ONLY) return;
     const Macro<T> m = node_macros<Q, T>(h, forced, p);
+    if (CLOSURE == LBM_CLOSURE_TRT) {
+        relax_trt<Q, T>(h, m, p.omega, p.omega_minus, forced);
+        return;
+    }
     T omega = p.omega;
     if (CLOSURE == LBM_CLOSURE_SMAGORINSKY) {
         T pi[6];
@@ -762,6 +804,9 @@ cudaError_t step_closure_x2(const Launch &L, const KParams<float> &kp)
     case LBM_CLOSURE_STREAM_ONLY:
         k_collide_stream_x2<Q, S, GEN, LBM_CLOSURE_STREAM_ONLY><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp);
         break;
+    case LBM_CLOSURE_TRT:
+        k_collide_stream_x2<Q, S, GEN, LBM_CLOSURE_TRT><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp);
+        break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -788,6 +833,9 @@ cudaError_t step_closure(const Launch &L, const KParams<typename Store<S>::T> &k
         break;
     case LBM_CLOSURE_STREAM_ONLY:
         k_collide_stream<Q, S, GEN, LBM_CLOSURE_STREAM_ONLY><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp);
+        break;
+    case LBM_CLOSURE_TRT:
+        k_collide_stream<Q, S, GEN, LBM_CLOSURE_TRT><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp);
         break;
     default: return cudaErrorInvalidValue;
     }
@@ -848,6 +896,10 @@ cudaError_t step_compact_q(const Launch &L, const lbm_params &p, const void *Ac,
         break;
     case LBM_CLOSURE_STREAM_ONLY:
         k_collide_stream_compact<Q, S, LBM_CLOSURE_STREAM_ONLY>
+            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
+        break;
+    case LBM_CLOSURE_TRT:
+        k_collide_stream_compact<Q, S, LBM_CLOSURE_TRT>
             <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
         break;
     default: return cudaErrorInvalidValue;

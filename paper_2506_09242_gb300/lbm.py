@@ -22,7 +22,7 @@ F64, F32, F16_SHIFTED, BF16_SHIFTED = 0, 1, 2, 3
 DTYPES = {"f64": F64, "f32": F32, "f16": F16_SHIFTED, "bf16": BF16_SHIFTED}
 TAG_FLUID, TAG_FORCED, TAG_SOLID, TAG_WALL0, NWALLS = 0, 1, 2, 3, 8
 NTAGS = TAG_WALL0 + NWALLS
-CLOSURE_BGK, CLOSURE_SMAGORINSKY, CLOSURE_MLP, CLOSURE_STREAM_ONLY = 0, 1, 2, 3
+CLOSURE_BGK, CLOSURE_SMAGORINSKY, CLOSURE_MLP, CLOSURE_STREAM_ONLY, CLOSURE_TRT = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_STATE", 5: "ERR_UNSTABLE",
                 6: "ERR_TIMEOUT"}
 
@@ -49,6 +49,7 @@ class Params(ctypes.Structure):
         ("cs_smag", ctypes.c_double),
         ("wall_u", (ctypes.c_double * 3) * NWALLS),
         ("rho_wall", ctypes.c_double),
+        ("trt_magic", ctypes.c_double),
     ]
 
 
@@ -89,6 +90,7 @@ SIGNATURES = {
     "lbm_init_equilibrium": (_I, [_P, _P, _P, _I]),
     "lbm_step": (_I, [_P, _I]),
     "lbm_step_count": (_I, [_P, ctypes.POINTER(_LL)]),
+    "lbm_use_graphs": (_I, [_P, _I]),
     "lbm_moments": (_I, [_P, _P, _P, _I]),
     "lbm_reduce": (_I, [_P, ctypes.POINTER(Reduction)]),
     "lbm_sync": (_I, [_P, _I]),
@@ -218,6 +220,7 @@ class Lattice:
         self.params = Params()
         self.params.tau = 1.0
         self.params.rho_wall = 1.0
+        self.params.trt_magic = 3.0 / 16.0
 
     # -- lifetime ------------------------------------------------------------
     def close(self):
@@ -256,7 +259,7 @@ class Lattice:
 
     # -- configuration -------------------------------------------------------
     def set_params(self, tau: float, *, force=(0.0, 0.0, 0.0), closure: int = CLOSURE_BGK, cs_smag: float = 0.0,
-                   wall_u=None, rho_wall: float = 1.0):
+                   wall_u=None, rho_wall: float = 1.0, trt_magic: float = 3.0 / 16.0):
         p = Params()
         p.tau = tau
         for a in range(3):
@@ -268,6 +271,7 @@ class Lattice:
                 for a in range(3):
                     p.wall_u[k][a] = v[a]
         p.rho_wall = rho_wall
+        p.trt_magic = trt_magic
         self._call("lbm_set_params", ctypes.byref(p))
         self.params = p
 
@@ -298,6 +302,9 @@ class Lattice:
 
     def step(self, n: int = 1):
         self._call("lbm_step", int(n))
+
+    def use_graphs(self, enable: bool = True):
+        self._call("lbm_use_graphs", int(bool(enable)))
 
     def step_count(self) -> int:
         v = ctypes.c_longlong()

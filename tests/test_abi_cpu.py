@@ -77,3 +77,24 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.lbm_step(None, 1) == lbm.ERR_ARG
     assert lib.lbm_destroy(None) == lbm.OK
     assert lib.lbm_sync(None, 0) == lbm.ERR_ARG
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: without the compiled library the binding raises."""
+    monkeypatch.setattr(lbm, "_lib", None)
+    monkeypatch.setattr(lbm, "_LIB_PATH", tmp_path / "missing.so")
+    with pytest.raises(ImportError):
+        lbm.load()
+    with pytest.raises(ImportError):
+        lbm.Lattice(8, 8, 8)
+
+
+def test_params_struct_matches_the_header():
+    """The binding's parameter struct has the header's fields in order."""
+    text = re.sub(r"/\*.*?\*/", "", (ROOT / "include" / "lbm.h").read_text(), flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\} lbm_params;", text).group(1)
+    names = re.findall(r"([a-z_]+)(?:\[[^\]]*\])*\s*;", body)
+    assert names == [f[0] for f in lbm.Params._fields_]
+    body = re.search(r"typedef struct \{([^}]*)\} lbm_reduction;", text).group(1)
+    names = re.findall(r"([a-z_]+)(?:\[[^\]]*\])*\s*;", body)
+    assert names == [f[0] for f in lbm.Reduction._fields_]

@@ -86,7 +86,7 @@ WALL_MIX = {"dense": dict(p_solid=0.15, p_forced=0.3, p_wall=0.06),
 
 @pytest.mark.parametrize("mix", ["dense", "list"])
 @pytest.mark.parametrize("Q", [19, 27])
-@pytest.mark.parametrize("closure", [lbm.CLOSURE_BGK, lbm.CLOSURE_SMAGORINSKY])
+@pytest.mark.parametrize("closure", [lbm.CLOSURE_BGK, lbm.CLOSURE_SMAGORINSKY, lbm.CLOSURE_TRT])
 def test_f64_tags_walls_force_ragged(Q, closure, mix):
     shape = (11, 13, 45)  # nx = 45: one full 32-block and a ragged tail; odd y, z
     tags = inp.random_tags(shape, seed=9, n_walls=3, **WALL_MIX[mix])
@@ -170,6 +170,68 @@ def test_compact_and_dense_paths_hand_over_the_state():
     _, ur = pa.moments(g)
     assert np.max(np.abs(ug - ur)) <= 1e-13
     lat.close()
+
+
+def test_trt_magic_poiseuille_on_the_gpu():
+    """TRT with Lambda = 3/16: the parabolic channel profile is exact at a tau
+    where BGK has a wall slip (FP64 storage)."""
+    H, g, tau = 16, 1e-5, 1.7
+    shape = (1, H + 2, 32)
+    tags = inp.channel_tags(32, H + 2, 1)
+    lat = make(shape, 19, "f64", tags, tau=tau, force=(g, 0.0, 0.0), closure=lbm.CLOSURE_TRT)
+    lat.init_equilibrium()
+    lat.step(30000)
+    _, u = lat.moments()
+    nu = (tau - 0.5) / 3.0
+    y = np.arange(1, H + 1, dtype=float)
+    exact = g / (2 * nu) * (y - 0.5) * (H + 0.5 - y)
+    assert np.max(np.abs(u[0, 0, 1:H + 1, :] - exact[:, None])) <= 1e-9 * exact.max()
+    lat.close()
+
+
+@pytest.mark.parametrize("mix", ["periodic", "dense", "list"])
+def test_graph_replay_is_bit_identical(mix):
+    """lbm_step replays pairs of steps as CUDA graphs; the result must be the
+    one of one launch per step, across odd counts and a parameter change."""
+    shape = (10, 9, 70)
+    tags = None if mix == "periodic" else inp.random_tags(shape, seed=41, n_walls=2, **WALL_MIX[mix])
+    rho, u = inp.random_velocity_field(shape, seed=42, amplitude=0.04)
+    out = []
+    for graphs in (False, True):
+        lat = make(shape, 19, "f32", tags, tau=0.7, force=(1e-4, 0, 0), wall_u=[(0.01, 0, 0), (0, 0.01, 0)])
+        lat.use_graphs(graphs)
+        lat.init_equilibrium(rho, u)
+        for n in (37, 1, 8):
+            lat.step(n)
+        lat.set_params(0.62, force=(1e-4, 0, 0), wall_u=[(0.01, 0, 0), (0, 0.01, 0)])
+        lat.step(9)
+        assert lat.step_count() == 55
+        out.append(lat.get_populations())
+        lat.close()
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 3, 1), (5, 1, 2), (2, 2, 3)])
+@pytest.mark.parametrize("Q", [19, 27])
+def test_degenerate_lattices(shape, Q):
+    """Lattices of one to a few nodes per axis: every neighbour wraps onto the
+    node itself or its row, in the scalar, tag and reduction kernels."""
+    _, w, _ = oracle.lattice(Q)
+    f0 = inp.random_populations(w, shape, seed=51, amplitude=0.1)
+    tags = inp.random_tags(shape, seed=52, p_solid=0.2, p_forced=0.3, p_wall=0.1, n_walls=1)
+    tags.flat[0] = oracle.FORCED  # keep at least one fluid node
+    params = dict(tau=0.8, force=(1e-3, -1e-3, 5e-4), wall_u=[(0.02, 0.01, 0.0)])
+    for t in (None, tags):
+        lat = make(shape, Q, "f64", t, **params)
+        lat.set_populations(f0)
+        lat.step(10)
+        prob = oracle_problem(shape, Q, t, **params)
+        g = prob.step(f0, 10)
+        assert max_rel(lat.get_populations(), g) <= 1e-12
+        red, ref = lat.reduce(), prob.reduce(g)
+        assert red["n_fluid"] == ref["n_fluid"]
+        assert red["mass"] == pytest.approx(ref["mass"], rel=1e-13)
+        lat.close()
 
 
 def test_all_solid_lattice_is_left_alone():
@@ -334,7 +396,8 @@ def test_half_storage_one_step(kind, Q, shape, mix):
 
 @pytest.mark.parametrize("shape", HALF_SHAPES)
 @pytest.mark.parametrize("kind", ["f16", "bf16"])
-@pytest.mark.parametrize("Q,closure", [(19, lbm.CLOSURE_BGK), (27, lbm.CLOSURE_BGK), (19, lbm.CLOSURE_SMAGORINSKY)])
+@pytest.mark.parametrize("Q,closure", [(19, lbm.CLOSURE_BGK), (27, lbm.CLOSURE_BGK), (19, lbm.CLOSURE_SMAGORINSKY),
+                                       (27, lbm.CLOSURE_TRT)])
 def test_half_storage_one_step_periodic(kind, Q, closure, shape):
     """All-fluid lattice: the kernel variant that reads no tags."""
     _, w, _ = oracle.lattice(Q)
@@ -394,7 +457,8 @@ def test_nan_injection_reports_unstable():
 
 def test_bad_params_rejected():
     lat = make((4, 4, 32), tau=0.8)
-    for kw in (dict(tau=0.5), dict(tau=float("nan")), dict(tau=0.7, closure=9), dict(tau=0.7, cs_smag=-1.0)):
+    for kw in (dict(tau=0.5), dict(tau=float("nan")), dict(tau=0.7, closure=9), dict(tau=0.7, cs_smag=-1.0),
+               dict(tau=0.7, closure=lbm.CLOSURE_TRT, trt_magic=0.0)):
         with pytest.raises(lbm.LBMError) as e:
             lat.set_params(**kw)
         assert e.value.status == lbm.ERR_ARG

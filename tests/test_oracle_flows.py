@@ -266,3 +266,33 @@ def test_sphere_porosity_follows_boolean_model():
         vol += np.count_nonzero((dx * dx + dy * dy + dz * dz).astype(float) <= r * r)
     expect = math.exp(-vol / np.prod(shape))
     assert por == pytest.approx(expect, abs=0.03)
+
+
+def test_trt_reduces_to_bgk_when_both_rates_match():
+    """Lambda = (tau - 1/2)^2 gives omega- = omega+: TRT is BGK."""
+    Q = 19
+    _, w, _ = oracle.lattice(Q)
+    shape = (6, 7, 8)
+    tags = inp.random_tags(shape, seed=2, p_solid=0.2, p_forced=0.3, p_wall=0.0)
+    f0 = inp.random_populations(w, shape, seed=3, amplitude=0.1)
+    tau = 0.73
+    kw = dict(tau=tau, force=(1e-4, 2e-5, 0.0))
+    bgk = oracle.Problem(Q, 8, 7, 6, tags, **kw).step(f0, 10)
+    trt = oracle.Problem(Q, 8, 7, 6, tags, closure=oracle.TRT, trt_magic=(tau - 0.5) ** 2, **kw).step(f0, 10)
+    assert np.max(np.abs(trt - bgk)) <= 1e-15
+
+
+@pytest.mark.parametrize("tau", [0.6, 1.0, 1.7])
+def test_trt_magic_poiseuille_is_exact_at_any_tau(tau):
+    """With Lambda = 3/16 halfway bounce-back is exact for the parabolic
+    profile whatever tau is (unlike BGK, exact only at tau = 1/2 + sqrt(3)/4)."""
+    H, g = 16, 1e-5
+    ny = H + 2
+    tags = inp.channel_tags(1, ny, 1)
+    prob = oracle.Problem(19, 1, ny, 1, tags, tau=tau, force=(g, 0.0, 0.0), closure=oracle.TRT, trt_magic=3.0 / 16.0)
+    f = prob.step(prob.init_equilibrium(), 30000)
+    _, u = prob.moments(f)
+    nu = (tau - 0.5) / 3.0
+    y = np.arange(1, H + 1, dtype=float)
+    exact = g / (2 * nu) * (y - 0.5) * (H + 0.5 - y)
+    assert np.max(np.abs(u[0, 0, 1:H + 1, 0] - exact)) <= 1e-9 * exact.max()
