@@ -63,6 +63,36 @@ def porous(n: int = 400, *, seed: int = 2506, rmin: float = 4.0, rmax: float = 1
             "history": hist[-5:]}
 
 
+def porous_tau_study(n: int = 200, *, taus=(0.6, 1.0, 1.5), closures=("bgk", "trt"), g: float = 1e-6,
+                     max_steps: int = 60_000, check_every: int = 2000, tol: float = 1e-5, seed: int = 2506) -> dict:
+    """Permeability of one random-sphere medium versus tau for BGK and TRT
+    (Lambda = 3/16): with TRT the halfway wall does not move with tau, so the
+    permeability should not change."""
+    import lbm_inputs as inp
+    centres, radii = inp.sphere_list((n, n, n), seed=seed, rmin=4.0, rmax=10.0, count=100_000)
+    out = {"n": n, "g": g, "runs": []}
+    for cl in closures:
+        kind = {"bgk": lbm.CLOSURE_BGK, "trt": lbm.CLOSURE_TRT}[cl]
+        for tau in taus:
+            with lbm.Lattice(n, n, n, lbm.D3Q19, "f32") as lat:
+                used, por = lat.geometry_spheres(centres, radii, 0.2, lbm.TAG_FORCED)
+                lat.set_params(tau, force=(g, 0.0, 0.0), closure=kind)
+                lat.init_equilibrium()
+                nu = (tau - 0.5) / 3.0
+                steps, prev, conv = 0, None, False
+                while steps < max_steps:
+                    lat.step(check_every)
+                    steps += check_every
+                    u_mean = lat.reduce()["vel"][0] / n ** 3
+                    if prev is not None and abs(u_mean - prev) <= tol * abs(u_mean):
+                        conv = True
+                        break
+                    prev = u_mean
+            out["runs"].append({"closure": cl, "tau": tau, "steps": steps, "converged": conv, "porosity": por,
+                                "permeability_voxel2": u_mean * nu / g})
+    return out
+
+
 def cavity(n: int = 256, *, re: float = 1000.0, u_lid: float = 0.1, steps: int = 10_000, dtype: str = "f32") -> dict:
     import lbm_inputs as inp
     tau = 0.5 + 3.0 * u_lid * n / re
@@ -136,7 +166,7 @@ def tgv_precision(n: int = 512, Q: int = 27, *, dtypes=("f64", "f32", "f16", "bf
 def main(argv=None):  # pragma: no cover - GPU workflow entry point
     import argparse
     ap = argparse.ArgumentParser(description="reference workloads")
-    ap.add_argument("which", choices=["porous", "cavity", "tgv_precision"])
+    ap.add_argument("which", choices=["porous", "porous_tau", "cavity", "tgv_precision"])
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--Q", type=int, default=27)
     ap.add_argument("--t-end", type=float, default=10.0)
@@ -144,6 +174,8 @@ def main(argv=None):  # pragma: no cover - GPU workflow entry point
     a = ap.parse_args(argv)
     if a.which == "porous":
         res = porous(a.n or 400)
+    elif a.which == "porous_tau":
+        res = porous_tau_study(a.n or 200)
     elif a.which == "cavity":
         res = cavity(a.n or 256)
     else:

@@ -5,8 +5,10 @@ through the library:
 - fine 256^3 Taylor-Green runs at Re = 800, 1600 and 3200;
 - box filtering by 4 into training samples for a 64^3 grid;
 - about 1500 Adam steps;
-- coarse 64^3 runs at Re = 1600 with plain BGK, Smagorinsky (Cs = 0.1) and
-  the learned closure.
+- an a-posteriori scale of the network output chosen on coarse runs at the
+  training Reynolds numbers;
+- coarse 64^3 runs at Re = 1600 with plain BGK, Smagorinsky (Cs = 0.1), the
+  raw learned closure and the calibrated one.
 
 Each coarse run is judged by the relative L2 error of its dissipation rate
 -dk/dt against the box-filtered fine run over 10 convective times. The
@@ -45,3 +47,7 @@ def test_learned_closure_beats_plain_bgk_on_the_coarse_grid():
     assert c["mlp"]["diverged_at_tc"] is None
     assert math.isfinite(mlp_err) and mlp_err < 0.5
     assert mlp_err < c["bgk"]["dissipation_rel_l2"]
+    cal = c["mlp_calibrated"]
+    assert cal["diverged_at_tc"] is None
+    assert cal["dissipation_rel_l2"] <= mlp_err
+    assert cal["dissipation_rel_l2"] < c["bgk"]["dissipation_rel_l2"]
