@@ -9,7 +9,8 @@ Default workload: periodic 3D Taylor-Green vortex, 512^3 nodes, D3Q19, FP32
 populations, Re = 1600, u0 = 0.04 (tau = 0.506112), BGK.  One benchmark step
 is ``inner`` lattice steps followed by the FP64 reduction (mass, momentum,
 kinetic energy) read back to the host, as a run that samples its kinetic
-energy does.  Inputs (two population arrays of 10.2 GB each) are far larger
+energy does; the reduction is fused into the last step
+(``lbm_step_reduce``).  Inputs (two population arrays of 10.2 GB each) are far larger
 than L2, so no flush is needed between steps.
 
 Also reported: ``e2e`` (each step uploads the initial fields from pinned host
@@ -208,8 +209,8 @@ def time_lattice(lat, steps: int, warmup: int, inner: int, sync_all=None):
     Returns (total_ms, mean collide-stream launch ms, reductions)."""
     import torch
     for _ in range(warmup):
-        lat.step(inner)
-        lat.reduce()
+        lat.step(inner - 1)
+        lat.step_reduce(1)
     torch.cuda.synchronize()
     if sync_all:
         sync_all()
@@ -221,15 +222,15 @@ def time_lattice(lat, steps: int, warmup: int, inner: int, sync_all=None):
     t0.record()
     for k in range(steps):
         ev[k][0].record()
-        lat.step(inner)
+        lat.step(inner - 1)
         ev[k][1].record()
-        reds.append(lat.reduce())
+        reds.append(lat.step_reduce(1))  # last step fused with the FP64 reduction
     t1.record()
     torch.cuda.synchronize()
     if sync_all:
         sync_all()
     total = t0.elapsed_time(t1)
-    kernel = sum(a.elapsed_time(b) for a, b in ev) / (steps * inner)
+    kernel = sum(a.elapsed_time(b) for a, b in ev) / (steps * (inner - 1))
     return total, kernel, reds
 
 
@@ -245,14 +246,12 @@ def time_e2e(lat, fields, steps: int, inner: int):
     rho_h = torch.from_numpy(np.ascontiguousarray(rho)).pin_memory()
     u_h = torch.from_numpy(np.ascontiguousarray(u)).pin_memory()
     lat.init_equilibrium(rho_h, u_h)  # warm-up of the staging buffers
-    lat.step(inner)
-    lat.reduce()
+    lat.step_reduce(inner)
     torch.cuda.synchronize()
     t = time.perf_counter()
     for _ in range(steps):
         lat.init_equilibrium(rho_h, u_h)
-        lat.step(inner)
-        lat.reduce()
+        lat.step_reduce(inner)
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t) * 1e3
     h2d = rho_h.numel() * 8 + u_h.numel() * 8
@@ -430,7 +429,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
         "config": {**desc, "inner_steps": args.inner, "parallelism": f"replicas{world}",
                    "l2": f"inputs larger than L2 ({alg_bytes / 1e9:.1f} GB moved per lattice step)",
-                   "step": f"{args.inner} lattice steps + FP64 reduction read back"},
+                   "step": f"{args.inner} lattice steps, the last fused with the FP64 reduction, read back"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "k_collide_stream", "kernel_ms": kernel_ms,
@@ -459,12 +458,14 @@ def main(argv=None):
     ap.add_argument("--workload", default="tgv512_d3q19")
     ap.add_argument("--dtype", default="f32", choices=sorted(SIZE))
     ap.add_argument("--closure", default="bgk", choices=CLOSURES)
-    ap.add_argument("--inner", type=int, default=20, help="lattice steps per benchmark step")
+    ap.add_argument("--inner", type=int, default=20, help="lattice steps per benchmark step (>= 2)")
     ap.add_argument("--ref-n", type=int, default=64, help="lattice size of the oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip variants, error table and CPU baseline")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.inner < 2:
+        raise SystemExit("--inner must be >= 2")
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

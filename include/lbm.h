@@ -166,6 +166,23 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u
  * without weights), CUDA (launch failure). */
 lbm_status lbm_step(lbm_ctx *ctx, int n);
 
+/* n >= 1 steps followed by the reduction of lbm_reduce, with the last step
+ * computing the reduction partials from the populations it writes, so the
+ * new state is not read a second time (the transform-reduce fusion of
+ * Sec. 2.2).  Same state as lbm_step(n).  The per-node density and
+ * velocity are the ones the last collision used (FP32 storage; lbm_reduce
+ * recomputes them from the stored populations, equal up to rounding), or
+ * the stored values read back (16-bit storage, as lbm_reduce).  Inside the
+ * step every operation is FP32: each block adds its 256 nodes (16-bit
+ * storage: 512) by a fixed shuffle tree, about 1e-6 relative on each part;
+ * the block partials are then added in FP64 in a fixed order.  FP64
+ * storage, lattices stepped on compact storage, the learned closure and
+ * pure streaming take the two separate passes (lbm_step, lbm_reduce).
+ * The first call allocates 48 bytes of partials per 256 nodes through the
+ * context's allocator.  Synchronizes.  Errors: ARG (n < 1), OOM, CUDA,
+ * UNSTABLE (as lbm_reduce, *out filled). */
+lbm_status lbm_step_reduce(lbm_ctx *ctx, int n, lbm_reduction *out);
+
 /* Enables (default) or disables replaying pairs of steps as CUDA graphs in
  * lbm_step.  With graphs, lbm_step(n >= 4) captures a two-step graph once
  * per kernel path and array orientation (again after lbm_set_params or

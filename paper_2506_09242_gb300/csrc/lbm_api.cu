@@ -53,6 +53,8 @@ struct lbm_ctx {
         unsigned long long version = 0;
     } graphs[4];
     unsigned long long version = 1;
+    float *fpart = nullptr;   // per-block FP32 partials of fused step-and-reduce launches
+    long long fpart_cap = 0;
     cudaStream_t stream = nullptr;
     lbm_allocator alloc{};
     bool has_alloc = false;
@@ -215,6 +217,40 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_final(const double *__re
         for (int k = 0; k < kRedSlots; ++k) out[k] = acc[k];
 }
 
+// First of two fixed-order passes over the FP32 block partials of a fused
+// step: block b adds the partials of its contiguous chunk in FP64 and roots
+// the maximum of |u|^2 (slot 9) in FP64, as the unfused reduction does.
+__global__ void __launch_bounds__(kRedThreads) k_reduce_chunks(const float *__restrict__ partials, long long n,
+                                                              double *__restrict__ out)
+{
+    const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+    const long long lo = blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+    double acc[kRedSlots];
+#pragma unroll
+    for (int k = 0; k < kRedSlots; ++k) acc[k] = 0.0;
+    for (long long b = lo + threadIdx.x; b < hi; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < kRedSlots; ++k) {
+            const double v = partials[b * kRedSlots + k];
+            acc[k] = (k == 9) ? fmax(acc[k], v) : acc[k] + v;
+        }
+    block_reduce_slots(acc);
+    if (threadIdx.x == 0) {
+        acc[9] = sqrt(acc[9]);
+#pragma unroll
+        for (int k = 0; k < kRedSlots; ++k) out[(long long)blockIdx.x * kRedSlots + k] = acc[k];
+    }
+}
+
+cudaError_t launch_reduce_partials(const float *partials, long long n, double *chunks, double *out, cudaStream_t s)
+{
+    k_reduce_chunks<<<kRedChunkBlocks, kRedThreads, 0, s>>>(partials, n, chunks);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_final<<<1, kRedThreads, 0, s>>>(chunks, kRedChunkBlocks, out);
+    return cudaGetLastError();
+}
+
 // Copies user tags into the padded internal array, flags fluid nodes that
 // pull from a SOLID or WALL neighbour, and counts tag values (slot LBM_NTAGS
 // counts invalid values).
@@ -359,6 +395,24 @@ static void dense_written(lbm_ctx *ctx)
         if (es_ != LBM_OK) return es_;              \
     } while (0)
 
+// The kRedSlots final sums as an lbm_reduction; UNSTABLE when some fluid
+// node had non-finite moments.
+static lbm_status fill_reduction(lbm_ctx *ctx, const double *r, lbm_reduction *out)
+{
+    out->n_fluid = (long long)r[10];
+    out->nonfinite = (long long)r[11];
+    out->mass = (double)(out->n_fluid - out->nonfinite) + r[0];
+    for (int a = 0; a < 3; ++a) {
+        out->mom[a] = r[1 + a];
+        out->vel[a] = r[4 + a];
+    }
+    out->ke = r[7];
+    out->ke_rho = r[8];
+    out->umax = r[9];
+    if (out->nonfinite) return fail(ctx, LBM_ERR_UNSTABLE, "%lld fluid nodes have non-finite moments", out->nonfinite);
+    return LBM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI.
 // ---------------------------------------------------------------------------
@@ -393,6 +447,7 @@ lbm_status lbm_destroy(lbm_ctx *ctx)
     dev_free(ctx, ctx->cA, (size_t)ctx->Q * ctx->nfp * ctx->elem);
     dev_free(ctx, ctx->cB, (size_t)ctx->Q * ctx->nfp * ctx->elem);
     dev_free(ctx, ctx->nbr, sizeof(int) * (size_t)(ctx->Q - 1) * ctx->nfp);
+    dev_free(ctx, ctx->fpart, sizeof(float) * kRedSlots * (size_t)ctx->fpart_cap);
     delete ctx;
     return LBM_OK;
 }
@@ -675,6 +730,43 @@ lbm_status lbm_step(lbm_ctx *ctx, int n)
     return run_steps(ctx, n, false);
 }
 
+lbm_status lbm_step_reduce(lbm_ctx *ctx, int n, lbm_reduction *out)
+{
+    if (!ctx || !out) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    if (n < 1) return fail(ctx, LBM_ERR_ARG, "n must be >= 1");
+    const bool fusable = !ctx->cA && ctx->dtype != LBM_F64 && ctx->params.closure != LBM_CLOSURE_MLP &&
+                         ctx->params.closure != LBM_CLOSURE_STREAM_ONLY;
+    if (!fusable) {  // compact storage, FP64, learned closure, pure streaming: separate passes
+        lbm_status st = lbm_step(ctx, n);
+        return st != LBM_OK ? st : lbm_reduce(ctx, out);
+    }
+    ENSURE_DENSE(ctx);
+    ctx->compact_valid = false;
+    lbm_status st = run_steps(ctx, n - 1, false);
+    if (st != LBM_OK) return st;
+    Launch L = make_launch(ctx);
+    const long long nparts = fused_partials(L, ctx->elem);
+    if (nparts > ctx->fpart_cap) {
+        dev_free(ctx, ctx->fpart, sizeof(float) * kRedSlots * (size_t)ctx->fpart_cap);
+        ctx->fpart = (float *)dev_alloc(ctx, sizeof(float) * kRedSlots * (size_t)nparts);
+        ctx->fpart_cap = ctx->fpart ? nparts : 0;
+        if (!ctx->fpart) return fail(ctx, LBM_ERR_OOM, "reduction partials allocation failed");
+    }
+    CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
+                 using S = std::remove_pointer_t<decltype(tag)>;
+                 return launch_step_reduce<S>(L, ctx->params, ctx->fpart);
+             }),
+             "fused collide-stream-reduce launch");
+    std::swap(ctx->A, ctx->B);
+    ++ctx->steps;
+    CUDA_TRY(ctx, launch_reduce_partials(ctx->fpart, nparts, ctx->partials, ctx->red_out, ctx->stream), "reduce");
+    double r[kRedSlots];
+    CUDA_TRY(ctx, cudaMemcpyAsync(r, ctx->red_out, sizeof r, cudaMemcpyDeviceToHost, ctx->stream), "reduce copy");
+    st = sync(ctx);
+    if (st != LBM_OK) return st;
+    return fill_reduction(ctx, r, out);
+}
+
 lbm_status lbm_use_graphs(lbm_ctx *ctx, int enable)
 {
     if (!ctx) return fail(ctx, LBM_ERR_ARG, "NULL context");
@@ -733,18 +825,7 @@ lbm_status lbm_reduce(lbm_ctx *ctx, lbm_reduction *out)
     CUDA_TRY(ctx, cudaMemcpyAsync(r, ctx->red_out, sizeof r, cudaMemcpyDeviceToHost, ctx->stream), "reduce copy");
     lbm_status s = sync(ctx);
     if (s != LBM_OK) return s;
-    out->n_fluid = (long long)r[10];
-    out->nonfinite = (long long)r[11];
-    out->mass = (double)(out->n_fluid - out->nonfinite) + r[0];
-    for (int a = 0; a < 3; ++a) {
-        out->mom[a] = r[1 + a];
-        out->vel[a] = r[4 + a];
-    }
-    out->ke = r[7];
-    out->ke_rho = r[8];
-    out->umax = r[9];
-    if (out->nonfinite) return fail(ctx, LBM_ERR_UNSTABLE, "%lld fluid nodes have non-finite moments", out->nonfinite);
-    return LBM_OK;
+    return fill_reduction(ctx, r, out);
 }
 
 lbm_status lbm_sync(lbm_ctx *ctx, int timeout_ms)

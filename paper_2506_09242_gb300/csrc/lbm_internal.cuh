@@ -56,24 +56,28 @@ template <> struct Store<double> {
     static __device__ __forceinline__ T ld(const double *p) { return __ldg(p); }
     static __device__ __forceinline__ void st(double *p, T v) { *p = v; }
     static __device__ __forceinline__ double from_f64(double v) { return v; }
+    static __device__ __forceinline__ T rt(T v) { return v; }  // value as stored
 };
 template <> struct Store<float> {
     using T = float;
     static __device__ __forceinline__ T ld(const float *p) { return __ldg(p); }
     static __device__ __forceinline__ void st(float *p, T v) { *p = v; }
     static __device__ __forceinline__ float from_f64(double v) { return (float)v; }
+    static __device__ __forceinline__ T rt(T v) { return v; }
 };
 template <> struct Store<__half> {
     using T = float;
     static __device__ __forceinline__ T ld(const __half *p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ void st(__half *p, T v) { *p = __float2half_rn(v); }
     static __device__ __forceinline__ __half from_f64(double v) { return __float2half_rn((float)v); }
+    static __device__ __forceinline__ T rt(T v) { return __half2float(__float2half_rn(v)); }
 };
 template <> struct Store<__nv_bfloat16> {
     using T = float;
     static __device__ __forceinline__ T ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, T v) { *p = __float2bfloat16_rn(v); }
     static __device__ __forceinline__ __nv_bfloat16 from_f64(double v) { return __float2bfloat16_rn((float)v); }
+    static __device__ __forceinline__ T rt(T v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 };
 
 // Fluid-node list (lattices that are mostly wall): link mask of each listed
@@ -133,6 +137,10 @@ struct Launch {
 
 // Per-storage-type launchers (one translation unit per type).
 template <typename S> cudaError_t launch_step(const Launch &L, const lbm_params &p);
+// One step that also writes per-block FP32 reduction partials of the new
+// state, kRedSlots floats per block (cudaErrorNotSupported for FP64 storage
+// and for closures without a fused variant).
+template <typename S> cudaError_t launch_step_reduce(const Launch &L, const lbm_params &p, float *partials);
 template <typename S>
 cudaError_t launch_step_compact(const Launch &L, const lbm_params &p, const void *Ac, void *Bc, const int *nbr,
                                 long long nfp);
@@ -149,6 +157,10 @@ template <typename S> cudaError_t launch_set_pop(const Launch &L, int i, const d
 cudaError_t launch_prepare_tags(int Q, const Grid &g, const uint8_t *user_tags, uint8_t *tags,
                                 unsigned long long *census, cudaStream_t s);
 cudaError_t launch_gather_tags(const Grid &g, const uint8_t *tags, uint8_t *out, cudaStream_t s);
+// Adds n FP32 block partials in FP64, in a fixed order (kRedChunkBlocks
+// chunks into chunks[], then one block), into out[kRedSlots].
+constexpr int kRedChunkBlocks = 304;  // 152 SMs x 2; <= kRedBlocks
+cudaError_t launch_reduce_partials(const float *partials, long long n, double *chunks, double *out, cudaStream_t s);
 
 // Fluid-node list (lbm_sparse.cu).
 cudaError_t launch_fluid_count(const Grid &g, const uint8_t *tags, int *count, cudaStream_t s);

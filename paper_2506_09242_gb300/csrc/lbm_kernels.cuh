@@ -58,6 +58,206 @@ struct Nbr {
 };
 
 // ---------------------------------------------------------------------------
+// Reduction helpers (FP64 sums over fluid nodes).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide reduction of kRedSlots values (slot 9 is a max, the rest sums)
+// for blocks of up to 256 threads; thread 0 ends with the result in acc.
+// Every thread of the block must call it.
+__device__ __forceinline__ void block_reduce_slots(double (&acc)[kRedSlots])
+{
+    __shared__ double sm[kRedThreads / 32][kRedSlots];
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nwarps = (blockDim.x * blockDim.y * blockDim.z + 31) / 32;
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < kRedSlots; ++k) acc[k] = (k == 9) ? warp_max(acc[k]) : warp_sum(acc[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < kRedSlots; ++k) sm[warp][k] = acc[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < kRedSlots; ++k) {
+            const double v = lane < nwarps ? sm[lane][k] : 0.0;
+            acc[k] = (k == 9) ? warp_max(v) : warp_sum(v);
+        }
+    }
+}
+
+// Per-thread accumulator of the reduction: plain FP64 for FP64 compute; for
+// FP32 compute a double-float pair (hi + lo) updated with Knuth's TwoSum,
+// which keeps about 44 significant bits while staying off the FP64 pipe
+// (GB300 has a low FP64 rate); partials are combined in FP64.
+template <typename T> struct Acc {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ double get() const { return v; }
+};
+template <> struct Acc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float s = hi + x;
+        const float bp = s - hi;
+        const float e = (hi - (s - bp)) + (x - bp);
+        hi = s;
+        lo += e;
+    }
+    __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+};
+
+// The sums of one thread's fluid nodes, in the slot order of the reduction.
+template <typename T> struct RedAcc {
+    Acc<T> dm, m[3], v[3], ke, ker;
+    T usq_max = T(0);
+    unsigned n_fluid = 0, n_bad = 0;
+    __device__ __forceinline__ void add(T d, const T (&u)[3])
+    {
+        const T rho = T(1) + d;
+        const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        ++n_fluid;
+        if (!isfinite(rho) || !isfinite(usq)) {
+            ++n_bad;
+            return;
+        }
+        dm.add(d);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            m[k].add(rho * u[k]);
+            v[k].add(u[k]);
+        }
+        ke.add(T(0.5) * usq);
+        ker.add(T(0.5) * rho * usq);
+        usq_max = usq > usq_max ? usq : usq_max;
+    }
+    __device__ __forceinline__ void slots(double (&acc)[kRedSlots]) const
+    {
+        acc[0] = dm.get();
+        for (int k = 0; k < 3; ++k) {
+            acc[1 + k] = m[k].get();
+            acc[4 + k] = v[k].get();
+        }
+        acc[7] = ke.get();
+        acc[8] = ker.get();
+        acc[9] = sqrt((double)usq_max);
+        acc[10] = (double)n_fluid;
+        acc[11] = (double)n_bad;
+    }
+};
+
+// Density deviation and velocity of one node from its post-collision set as
+// it is stored (rounded to the storage type), the same quantities
+// node_moments reads back from memory.
+template <int Q, typename S>
+__device__ __forceinline__ void stored_moments(const typename Store<S>::T (&h)[Q], bool forced,
+                                               const KParams<typename Store<S>::T> &p, typename Store<S>::T &drho,
+                                               typename Store<S>::T (&u)[3])
+{
+    using T = typename Store<S>::T;
+    T d = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T v = Store<S>::rt(h[i]);
+        d += v;
+        if (cvel(i, 0)) jx += cvel(i, 0) > 0 ? v : -v;
+        if (cvel(i, 1)) jy += cvel(i, 1) > 0 ? v : -v;
+        if (cvel(i, 2)) jz += cvel(i, 2) > 0 ? v : -v;
+    }
+    const T rho = T(1) + d;
+    if (forced) {
+        jx -= T(0.5) * rho * p.force[0];
+        jy -= T(0.5) * rho * p.force[1];
+        jz -= T(0.5) * rho * p.force[2];
+    }
+    const T inv = T(1) / rho;
+    drho = d;
+    u[0] = jx * inv;
+    u[1] = jy * inv;
+    u[2] = jz * inv;
+}
+
+// Reduction slots of the nodes one thread owns inside a fused step, in FP32.
+// GB300 runs FP64 at 1/64 of the FP32 rate, so a step kernel that did even
+// a few dozen FP64 operations per block of 256 nodes would be bound by them;
+// here every per-node and per-block operation is FP32, and the block partials
+// are added in FP64 by a separate pass over the (small) partial buffer.
+struct NodeSums {
+    float s[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dmass, mom[3], vel[3], ke, ke_rho
+    float usq_max = 0.f;
+    unsigned n_fluid = 0, n_bad = 0;
+    __device__ __forceinline__ void add(float d, const float (&u)[3])
+    {
+        const float rho = 1.f + d;
+        const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        ++n_fluid;
+        if (!isfinite(rho) || !isfinite(usq)) {
+            ++n_bad;
+            return;
+        }
+        s[0] += d;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            s[1 + k] += rho * u[k];
+            s[4 + k] += u[k];
+        }
+        s[7] += 0.5f * usq;
+        s[8] += 0.5f * rho * usq;
+        usq_max = fmaxf(usq_max, usq);
+    }
+};
+
+// Writes the block's kRedSlots partial (slot 9 = max |u|^2, rooted in FP64
+// when the partials are combined) to out[0..kRedSlots).  Lanes are added by a shuffle tree, warps in a fixed
+// order by one thread each slot, so the result does not depend on
+// scheduling.  Every thread of the block must call it (no early returns).
+__device__ __forceinline__ void block_partial_f32(const NodeSums &ns, float *__restrict__ out)
+{
+    __shared__ float wsum[kStepThreads / 32][kRedSlots];
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = (blockDim.x * blockDim.y + 31) / 32;
+    float v[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v[k] = ns.s[k];
+    float mx = ns.usq_max;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    const unsigned nf = __reduce_add_sync(0xffffffffu, ns.n_fluid);
+    const unsigned nb = __reduce_add_sync(0xffffffffu, ns.n_bad);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) wsum[warp][k] = v[k];
+        wsum[warp][9] = mx;
+        wsum[warp][10] = (float)nf;  // at most 2 x kStepThreads: exact
+        wsum[warp][11] = (float)nb;
+    }
+    __syncthreads();
+    if (tid < kRedSlots) {
+        float a = wsum[0][tid];
+        for (int w = 1; w < nwarps; ++w) a = (tid == 9) ? fmaxf(a, wsum[w][tid]) : a + wsum[w][tid];
+        out[tid] = a;
+    }
+}
+
+__device__ __forceinline__ long long linear_block() { return blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z); }
+
+// ---------------------------------------------------------------------------
 // Boundary rules for one fluid node next to a wall (tag bit kNearWall):
 // halfway bounce-back from a SOLID source, h_i(x) = h*_opp(i)(x); Ladd's
 // moving-wall term from a WALL_k source, + 6 w_i rho_wall (c_i . u_wall_k).
@@ -220,14 +420,16 @@ __device__ __forceinline__ void relax_trt(T (&h)[Q], const Macro<T> &m, T wp, T 
     }
 }
 
+// Returns the density and velocity the collision used (mass and momentum
+// invariants of the new state).
 template <int Q, typename T, int CLOSURE>
-__device__ __forceinline__ void collide_node(T (&h)[Q], bool forced, const KParams<T> &p)
+__device__ __forceinline__ Macro<T> collide_node(T (&h)[Q], bool forced, const KParams<T> &p)
 {
-    if (CLOSURE == LBM_CLOSURE_STREAM_ONLY) return;
+    if (CLOSURE == LBM_CLOSURE_STREAM_ONLY) return Macro<T>{};
     const Macro<T> m = node_macros<Q, T>(h, forced, p);
     if (CLOSURE == LBM_CLOSURE_TRT) {
         relax_trt<Q, T>(h, m, p.omega, p.omega_minus, forced);
-        return;
+        return m;
     }
     T omega = p.omega;
     if (CLOSURE == LBM_CLOSURE_SMAGORINSKY) {
@@ -238,32 +440,29 @@ __device__ __forceinline__ void collide_node(T (&h)[Q], bool forced, const KPara
         omega = T(1) / te;
     }
     relax<Q, T>(h, m, omega, forced);
+    return m;
 }
 
-// ---------------------------------------------------------------------------
-// Fused collide-and-stream (pull, two populations), one node per thread.
-//   GENERAL: tags are read (bounce-back, Ladd walls, forced nodes); without
-//            it every node is a plain fluid node and no tag byte is touched.
-//   CLOSURE: LBM_CLOSURE_BGK, _SMAGORINSKY or _STREAM_ONLY.
-// ---------------------------------------------------------------------------
-template <int Q, typename S, bool GENERAL, int CLOSURE>
-__global__ void __launch_bounds__(kStepThreads)
-    k_collide_stream(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ tags, Grid g,
-                     KParams<typename Store<S>::T> p)
+// The work of one node (x, y, z): pull, boundary rules, collision, store.
+// Solid and wall nodes are never updated.  With REDUCE (FP32 compute only)
+// the node's density deviation and velocity are added to ns: the values the
+// collision used where the storage is FP32 (mass and momentum are collision
+// invariants), otherwise recomputed from the post-collision set rounded to
+// the storage type, which is what a later pass over memory would read.
+template <int Q, typename S, bool GENERAL, int CLOSURE, bool REDUCE>
+__device__ __forceinline__ void collide_stream_node(const S *__restrict__ A, S *__restrict__ B,
+                                                    const uint8_t *__restrict__ tags, const Grid &g,
+                                                    const KParams<typename Store<S>::T> &p, int x, int y, int z,
+                                                    NodeSums &ns)
 {
     using T = typename Store<S>::T;
     using St = Store<S>;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= g.nx || y >= g.ny) return;
-
     Nbr nb;
     nb.init(g, x, y, z);
     unsigned t = 0;
     if (GENERAL) {
         t = tags[nb.self];
-        if (is_wall_tag(t & kTagMask)) return;  // solid and wall nodes are never updated
+        if (is_wall_tag(t & kTagMask)) return;
     }
 
     // Pull: h_i(x) = h*_i(x - c_i).
@@ -272,10 +471,41 @@ __global__ void __launch_bounds__(kStepThreads)
     for (int i = 0; i < Q; ++i) h[i] = St::ld(A + (long long)i * g.sN + nb.src(i));
     if (GENERAL && (t & kNearWall)) apply_walls<Q, S>(h, A, tags, g, nb, p);
 
-    collide_node<Q, T, CLOSURE>(h, GENERAL && (t & kTagMask) == LBM_TAG_FORCED, p);
+    const bool forced = GENERAL && (t & kTagMask) == LBM_TAG_FORCED;
+    const Macro<T> m = collide_node<Q, T, CLOSURE>(h, forced, p);
+    if constexpr (REDUCE) {
+        static_assert(sizeof(T) == 4, "fused reductions are FP32-compute only");
+        if constexpr (sizeof(S) == sizeof(T)) {
+            const float u[3] = {m.ux, m.uy, m.uz};
+            ns.add(m.drho, u);
+        } else {
+            T d, u[3];
+            stored_moments<Q, S>(h, forced, p, d, u);
+            ns.add(d, u);
+        }
+    }
 
 #pragma unroll
     for (int i = 0; i < Q; ++i) St::st(B + (long long)i * g.sN + nb.self, h[i]);
+}
+
+// Fused collide-and-stream (pull, two populations), one node per thread.
+//   GENERAL: tags are read (bounce-back, Ladd walls, forced nodes); without
+//            it every node is a plain fluid node and no tag byte is touched.
+//   CLOSURE: LBM_CLOSURE_BGK, _SMAGORINSKY, _STREAM_ONLY or _TRT.
+//   REDUCE:  also writes this block's reduction partial of the new state to
+//            partials[linear block index][0..kRedSlots).
+template <int Q, typename S, bool GENERAL, int CLOSURE, bool REDUCE>
+__global__ void __launch_bounds__(kStepThreads)
+    k_collide_stream(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ tags, Grid g,
+                     KParams<typename Store<S>::T> p, float *__restrict__ partials)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    NodeSums ns;
+    if (x < g.nx && y < g.ny) collide_stream_node<Q, S, GENERAL, CLOSURE, REDUCE>(A, B, tags, g, p, x, y, z, ns);
+    if constexpr (REDUCE) block_partial_f32(ns, partials + linear_block() * kRedSlots);
 }
 
 // Ladd's moving-wall term 6 w_i rho_wall (c_i . u_wall) of the wall whose tag
@@ -421,16 +651,12 @@ template <> struct Pair<float> {
     }
 };
 
-template <int Q, typename S, bool GENERAL, int CLOSURE>
-__global__ void __launch_bounds__(kStepThreads)
-    k_collide_stream_x2(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ tags, Grid g,
-                        KParams<float> p)
+template <int Q, typename S, bool GENERAL, int CLOSURE, bool REDUCE>
+__device__ __forceinline__ void collide_stream_pair(const S *__restrict__ A, S *__restrict__ B,
+                                                    const uint8_t *__restrict__ tags, const Grid &g,
+                                                    const KParams<float> &p, int pair, int y, int z, NodeSums &ns)
 {
     using St = Store<S>;
-    const int pair = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (y >= g.ny) return;  // uniform over the warp: a warp lies in one row
     const unsigned lane = threadIdx.x & 31u;
     const int x0 = 2 * pair;
     const bool va = x0 < g.nx, vb = x0 + 1 < g.nx;
@@ -516,6 +742,17 @@ __global__ void __launch_bounds__(kStepThreads)
         }
         collide_node<Q, float, CLOSURE>(ta_, fa, p);
         collide_node<Q, float, CLOSURE>(tb_, fb, p);
+        if constexpr (REDUCE) {
+            float d, u[3];
+            if (act_a) {
+                stored_moments<Q, S>(ta_, fa, p, d, u);
+                ns.add(d, u);
+            }
+            if (act_b) {
+                stored_moments<Q, S>(tb_, fb, p, d, u);
+                ns.add(d, u);
+            }
+        }
 #pragma unroll
         for (int i = 0; i < Q; ++i) h[i] = make_float2(ta_[i], tb_[i]);
     }
@@ -530,6 +767,21 @@ __global__ void __launch_bounds__(kStepThreads)
             if (act_b) St::st(B + (long long)i * g.sN + self + 1, h[i].y);
         }
     }
+}
+
+template <int Q, typename S, bool GENERAL, int CLOSURE, bool REDUCE>
+__global__ void __launch_bounds__(kStepThreads)
+    k_collide_stream_x2(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ tags, Grid g,
+                        KParams<float> p, float *__restrict__ partials)
+{
+    const int pair = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    NodeSums ns;
+    // y >= ny is uniform over a warp (a warp lies in one row), so skipping
+    // those warps keeps every shuffle of the node work warp-complete
+    if (y < g.ny) collide_stream_pair<Q, S, GENERAL, CLOSURE, REDUCE>(A, B, tags, g, p, pair, y, z, ns);
+    if constexpr (REDUCE) block_partial_f32(ns, partials + linear_block() * kRedSlots);
 }
 
 // ---------------------------------------------------------------------------
@@ -593,104 +845,39 @@ __global__ void __launch_bounds__(kStepThreads)
 
 // ---------------------------------------------------------------------------
 // Reduction: FP64 sums over fluid nodes.  Pass 1 writes one partial per block
-// (fixed grid, grid-stride over nodes), pass 2 adds the partials in a fixed
-// order, so the result does not depend on scheduling.
+// (a fixed grid of at most one resident wave; block b sweeps one contiguous
+// range of the padded node index, its threads side by side), pass 2 adds the
+// partials in a fixed order, so the result does not depend on scheduling.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ double warp_max(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// Block-wide reduction of kRedSlots values (slot 9 is a max, the rest sums);
-// thread 0 ends with the result in acc.
-__device__ __forceinline__ void block_reduce_slots(double (&acc)[kRedSlots])
-{
-    __shared__ double sm[kRedThreads / 32][kRedSlots];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < kRedSlots; ++k) acc[k] = (k == 9) ? warp_max(acc[k]) : warp_sum(acc[k]);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < kRedSlots; ++k) sm[warp][k] = acc[k];
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int k = 0; k < kRedSlots; ++k) {
-            double v = lane < kRedThreads / 32 ? sm[lane][k] : (k == 9 ? 0.0 : 0.0);
-            acc[k] = (k == 9) ? warp_max(v) : warp_sum(v);
-        }
-    }
-}
-
-// Per-thread accumulator of the reduction: plain FP64 for FP64 compute; for
-// FP32 compute a double-float pair (hi + lo) updated with Knuth's TwoSum,
-// which keeps about 44 significant bits while staying off the FP64 pipe
-// (GB300 has a low FP64 rate); partials are combined in FP64.
-template <typename T> struct Acc {
-    double v = 0.0;
-    __device__ __forceinline__ void add(double x) { v += x; }
-    __device__ __forceinline__ double get() const { return v; }
-};
-template <> struct Acc<float> {
-    float hi = 0.f, lo = 0.f;
-    __device__ __forceinline__ void add(float x)
-    {
-        const float s = hi + x;
-        const float bp = s - hi;
-        const float e = (hi - (s - bp)) + (x - bp);
-        hi = s;
-        lo += e;
-    }
-    __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
-};
-
 template <int Q, typename S, bool GENERAL>
 __global__ void __launch_bounds__(kRedThreads)
     k_reduce(const S *__restrict__ A, const uint8_t *__restrict__ tags, Grid g, KParams<typename Store<S>::T> p,
              double *__restrict__ partials)
 {
     using T = typename Store<S>::T;
-    Acc<T> a_dm, a_m[3], a_v[3], a_ke, a_ker;
-    T usq_max = T(0);
-    unsigned n_fluid = 0, n_bad = 0;
-    const long long total = (long long)g.nz * g.ny * g.px;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(idx % g.px);
-        if (x >= g.nx) continue;
-        const int off = (int)idx;
-        const unsigned t = GENERAL ? (tags[off] & kTagMask) : 0u;
-        if (is_wall_tag(t)) continue;
-        T d, v[3];
-        node_moments<Q, S>(A, g.sN, off, t == LBM_TAG_FORCED, p, d, v);
-        const T rho = T(1) + d;
-        const T usq = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-        ++n_fluid;
-        if (!isfinite(rho) || !isfinite(usq)) {
-            ++n_bad;
-            continue;
+    RedAcc<T> ra;
+    const long long total = (long long)g.nz * g.ny * g.px;  // < 2^31 - 256
+    const long long chunk = ((total + gridDim.x - 1) / gridDim.x + 31) & ~31ll;
+    const long long lo = blockIdx.x * chunk;
+    const int hi = (int)(lo + chunk < total ? lo + chunk : total);
+    if (lo < total) {
+        int idx = (int)lo + threadIdx.x;
+        int x = idx % g.px;
+        for (; idx < hi; idx += blockDim.x) {
+            if (x < g.nx) {
+                const unsigned t = GENERAL ? (tags[idx] & kTagMask) : 0u;
+                if (!is_wall_tag(t)) {
+                    T d, v[3];
+                    node_moments<Q, S>(A, g.sN, idx, t == LBM_TAG_FORCED, p, d, v);
+                    ra.add(d, v);
+                }
+            }
+            x += blockDim.x;
+            while (x >= g.px) x -= g.px;
         }
-        a_dm.add(d);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            a_m[k].add(rho * v[k]);
-            a_v[k].add(v[k]);
-        }
-        a_ke.add(T(0.5) * usq);
-        a_ker.add(T(0.5) * rho * usq);
-        usq_max = usq > usq_max ? usq : usq_max;
     }
-    double acc[kRedSlots] = {a_dm.get(),  a_m[0].get(),         a_m[1].get(),         a_m[2].get(),
-                             a_v[0].get(), a_v[1].get(),         a_v[2].get(),         a_ke.get(),
-                             a_ker.get(),  sqrt((double)usq_max), (double)n_fluid, (double)n_bad};
+    double acc[kRedSlots];
+    ra.slots(acc);
     block_reduce_slots(acc);
     if (threadIdx.x == 0)
 #pragma unroll
@@ -789,57 +976,87 @@ inline void pair_launch_shape(const Grid &g, dim3 &grid, dim3 &block)
     grid = dim3((pairs + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
 }
 
-template <int Q, typename S, bool GEN>
-cudaError_t step_closure_x2(const Launch &L, const KParams<float> &kp)
+template <int Q, typename S, bool GEN, bool RED>
+cudaError_t step_closure_x2(const Launch &L, const KParams<float> &kp, float *partials)
 {
     dim3 grid, block;
     pair_launch_shape(L.g, grid, block);
     const S *A = (const S *)L.A;
     S *B = (S *)L.B;
     switch (L.closure) {
-    case LBM_CLOSURE_BGK: k_collide_stream_x2<Q, S, GEN, LBM_CLOSURE_BGK><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp); break;
-    case LBM_CLOSURE_SMAGORINSKY:
-        k_collide_stream_x2<Q, S, GEN, LBM_CLOSURE_SMAGORINSKY><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp);
+    case LBM_CLOSURE_BGK:
+        k_collide_stream_x2<Q, S, GEN, LBM_CLOSURE_BGK, RED><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, partials);
         break;
-    case LBM_CLOSURE_STREAM_ONLY:
-        k_collide_stream_x2<Q, S, GEN, LBM_CLOSURE_STREAM_ONLY><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp);
+    case LBM_CLOSURE_SMAGORINSKY:
+        k_collide_stream_x2<Q, S, GEN, LBM_CLOSURE_SMAGORINSKY, RED>
+            <<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, partials);
         break;
     case LBM_CLOSURE_TRT:
-        k_collide_stream_x2<Q, S, GEN, LBM_CLOSURE_TRT><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp);
+        k_collide_stream_x2<Q, S, GEN, LBM_CLOSURE_TRT, RED><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, partials);
+        break;
+    case LBM_CLOSURE_STREAM_ONLY:
+        if constexpr (RED) return cudaErrorNotSupported;
+        k_collide_stream_x2<Q, S, GEN, LBM_CLOSURE_STREAM_ONLY, false>
+            <<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, nullptr);
         break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-template <int Q, typename S, bool GEN>
-cudaError_t step_closure(const Launch &L, const KParams<typename Store<S>::T> &kp, dim3 grid, dim3 block)
+// RED: fused step-and-reduce (FP32 compute; BGK, Smagorinsky and TRT).
+template <int Q, typename S, bool GEN, bool RED>
+cudaError_t step_closure(const Launch &L, const KParams<typename Store<S>::T> &kp, dim3 grid, dim3 block,
+                         float *partials)
 {
-    const S *A = (const S *)L.A;
-    S *B = (S *)L.B;
-    if (L.closure == LBM_CLOSURE_MLP) {
-        if (!L.mlp_image) return cudaErrorInvalidValue;
-        k_collide_stream_mlp<Q, S, GEN>
-            <<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, (const MlpSmem *)L.mlp_image);
+    if constexpr (RED && sizeof(typename Store<S>::T) != 4) {
+        return cudaErrorNotSupported;
+    } else {
+        const S *A = (const S *)L.A;
+        S *B = (S *)L.B;
+        if (L.closure == LBM_CLOSURE_MLP) {
+            if (RED) return cudaErrorNotSupported;
+            if (!L.mlp_image) return cudaErrorInvalidValue;
+            k_collide_stream_mlp<Q, S, GEN>
+                <<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, (const MlpSmem *)L.mlp_image);
+            return cudaGetLastError();
+        }
+        if constexpr (use_pairs<S>()) {
+            if (L.g.px >= 64) return step_closure_x2<Q, S, GEN, RED>(L, kp, partials);
+        }
+        switch (L.closure) {
+        case LBM_CLOSURE_BGK:
+            k_collide_stream<Q, S, GEN, LBM_CLOSURE_BGK, RED>
+                <<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, partials);
+            break;
+        case LBM_CLOSURE_SMAGORINSKY:
+            k_collide_stream<Q, S, GEN, LBM_CLOSURE_SMAGORINSKY, RED>
+                <<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, partials);
+            break;
+        case LBM_CLOSURE_TRT:
+            k_collide_stream<Q, S, GEN, LBM_CLOSURE_TRT, RED>
+                <<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, partials);
+            break;
+        case LBM_CLOSURE_STREAM_ONLY:
+            if constexpr (RED) return cudaErrorNotSupported;
+            k_collide_stream<Q, S, GEN, LBM_CLOSURE_STREAM_ONLY, false>
+                <<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, nullptr);
+            break;
+        default: return cudaErrorInvalidValue;
+        }
         return cudaGetLastError();
     }
-    if constexpr (use_pairs<S>()) {
-        if (L.g.px >= 64) return step_closure_x2<Q, S, GEN>(L, kp);
-    }
-    switch (L.closure) {
-    case LBM_CLOSURE_BGK: k_collide_stream<Q, S, GEN, LBM_CLOSURE_BGK><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp); break;
-    case LBM_CLOSURE_SMAGORINSKY:
-        k_collide_stream<Q, S, GEN, LBM_CLOSURE_SMAGORINSKY><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp);
-        break;
-    case LBM_CLOSURE_STREAM_ONLY:
-        k_collide_stream<Q, S, GEN, LBM_CLOSURE_STREAM_ONLY><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp);
-        break;
-    case LBM_CLOSURE_TRT:
-        k_collide_stream<Q, S, GEN, LBM_CLOSURE_TRT><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp);
-        break;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+}
+
+// Number of blocks (= partials) a fused step-and-reduce launch writes.
+inline long long fused_partials(const Launch &L, size_t elem)
+{
+    dim3 grid, block;
+    if (elem == 2 && L.g.px >= 64)
+        pair_launch_shape(L.g, grid, block);
+    else
+        node_launch_shape(L.g, grid, block);
+    return (long long)grid.x * grid.y * grid.z;
 }
 
 template <int Q, typename S> cudaError_t step_q(const Launch &L, const lbm_params &p)
@@ -847,13 +1064,40 @@ template <int Q, typename S> cudaError_t step_q(const Launch &L, const lbm_param
     dim3 grid, block;
     node_launch_shape(L.g, grid, block);
     const auto kp = make_kparams<typename Store<S>::T>(Q, p);
-    return L.general ? step_closure<Q, S, true>(L, kp, grid, block) : step_closure<Q, S, false>(L, kp, grid, block);
+    return L.general ? step_closure<Q, S, true, false>(L, kp, grid, block, nullptr)
+                     : step_closure<Q, S, false, false>(L, kp, grid, block, nullptr);
 }
 
+template <int Q, typename S> cudaError_t step_reduce_q(const Launch &L, const lbm_params &p, float *partials)
+{
+    dim3 grid, block;
+    node_launch_shape(L.g, grid, block);
+    const auto kp = make_kparams<typename Store<S>::T>(Q, p);
+    return L.general ? step_closure<Q, S, true, true>(L, kp, grid, block, partials)
+                     : step_closure<Q, S, false, true>(L, kp, grid, block, partials);
+}
+
+// Blocks of `threads` threads of `kernel` that fit on the device at once.
+template <typename K> int resident_blocks(K kernel, int threads)
+{
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0) != cudaSuccess)
+        return 0;
+    return sms * occ;
+}
+
+// nblocks (<= kRedBlocks) is cut to one resident wave: every block then
+// sweeps the same number of nodes at the same time, with no second, partly
+// filled wave.
 template <int Q, typename S>
 cudaError_t reduce_q(const Launch &L, const lbm_params &p, double *partials, int nblocks, double *out)
 {
     const auto kp = make_kparams<typename Store<S>::T>(Q, p);
+    const int wave = L.general ? resident_blocks(k_reduce<Q, S, true>, kRedThreads)
+                               : resident_blocks(k_reduce<Q, S, false>, kRedThreads);
+    if (wave > 0 && nblocks > wave) nblocks = wave;
     if (L.general)
         k_reduce<Q, S, true><<<nblocks, kRedThreads, 0, L.stream>>>((const S *)L.A, L.tags, L.g, kp, partials);
     else
@@ -908,6 +1152,10 @@ cudaError_t step_compact_q(const Launch &L, const lbm_params &p, const void *Ac,
 }
 
 #define LBM_DEFINE_LAUNCHERS(S)                                                                              \
+    template <> cudaError_t launch_step_reduce<S>(const Launch &L, const lbm_params &p, float *partials)     \
+    {                                                                                                        \
+        return L.Q == 19 ? step_reduce_q<19, S>(L, p, partials) : step_reduce_q<27, S>(L, p, partials);     \
+    }                                                                                                        \
     template <>                                                                                              \
     cudaError_t launch_step_compact<S>(const Launch &L, const lbm_params &p, const void *Ac, void *Bc,       \
                                        const int *nbr, long long nfp)                                        \

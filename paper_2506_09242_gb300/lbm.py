@@ -91,6 +91,7 @@ SIGNATURES = {
     "lbm_step": (_I, [_P, _I]),
     "lbm_step_count": (_I, [_P, ctypes.POINTER(_LL)]),
     "lbm_use_graphs": (_I, [_P, _I]),
+    "lbm_step_reduce": (_I, [_P, _I, ctypes.POINTER(Reduction)]),
     "lbm_moments": (_I, [_P, _P, _P, _I]),
     "lbm_reduce": (_I, [_P, ctypes.POINTER(Reduction)]),
     "lbm_sync": (_I, [_P, _I]),
@@ -327,6 +328,15 @@ class Lattice:
     def reduce(self) -> dict:
         out = Reduction()
         st = load().lbm_reduce(self._ctx, ctypes.byref(out))
+        if st == ERR_UNSTABLE:
+            raise UnstableError(st, load().lbm_last_error(self._ctx).decode(), out.as_dict())
+        _check(st, self._ctx)
+        return out.as_dict()
+
+    def step_reduce(self, n: int) -> dict:
+        """n steps and the reduction of the new state, fused into the last step."""
+        out = Reduction()
+        st = load().lbm_step_reduce(self._ctx, int(n), ctypes.byref(out))
         if st == ERR_UNSTABLE:
             raise UnstableError(st, load().lbm_last_error(self._ctx).decode(), out.as_dict())
         _check(st, self._ctx)

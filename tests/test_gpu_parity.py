@@ -234,6 +234,49 @@ def test_degenerate_lattices(shape, Q):
         lat.close()
 
 
+@pytest.mark.parametrize("kind", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("mix", ["periodic", "dense", "list"])
+@pytest.mark.parametrize("closure", [lbm.CLOSURE_BGK, lbm.CLOSURE_TRT])
+def test_fused_step_reduce_matches_separate_passes(kind, mix, closure):
+    """lbm_step_reduce computes the reduction inside the last step: the state
+    must be bit-identical to lbm_step and the counts exact.  FP32/FP64 take
+    the collision's own density and velocity (equal to the stored moments up
+    to rounding), 16-bit storage the stored values (the same per-node moments
+    as lbm_reduce); the sums differ in their grouping."""
+    shape = (12, 33, 96)  # many blocks: partials pass through both combine stages
+    tags = None if mix == "periodic" else inp.random_tags(shape, seed=61, n_walls=2, **WALL_MIX[mix])
+    rho, u = inp.random_velocity_field(shape, seed=62, amplitude=0.05)
+    params = dict(tau=0.66, force=(2e-4, 0, 0), wall_u=[(0.02, 0, 0), (0, 0, 0.01)], closure=closure)
+    outs = []
+    for fused in (False, True):
+        lat = make(shape, 19, kind, tags, **params)
+        lat.init_equilibrium(rho, u)
+        if fused:
+            red = lat.step_reduce(7)
+        else:
+            lat.step(7)
+            red = lat.reduce()
+        outs.append((lat.get_populations(), red))
+        lat.close()
+    (fa, ra), (fb, rb) = outs
+    assert np.array_equal(fa, fb)
+    assert ra["n_fluid"] == rb["n_fluid"] and ra["nonfinite"] == rb["nonfinite"] == 0
+    # FP64 storage takes the separate passes; 32/16-bit storage adds each
+    # block's 256 (16-bit: 512) nodes in FP32 by a shuffle tree (about 1e-6
+    # relative on each part, smaller on the total) and the block partials in
+    # FP64; FP32 per-node moments differ from the stored ones by FP32 rounding
+    rel = 1e-12 if kind == "f64" else 1e-6
+    assert rb["umax"] == pytest.approx(ra["umax"], rel=rel)
+    if kind in ("f16", "bf16"):
+        assert ra["umax"] == rb["umax"]
+    for key in ("mass", "ke", "ke_rho"):
+        assert rb[key] == pytest.approx(ra[key], rel=rel)
+    scale = ra["n_fluid"] * ra["umax"]
+    for a in range(3):
+        assert abs(rb["mom"][a] - ra["mom"][a]) <= rel * scale
+        assert abs(rb["vel"][a] - ra["vel"][a]) <= rel * scale
+
+
 def test_all_solid_lattice_is_left_alone():
     shape = (4, 5, 40)
     _, w, _ = oracle.lattice(19)
