@@ -70,10 +70,11 @@ def tgv_fields(n: int):
 CLOSURES = ("bgk", "smagorinsky", "mlp")
 
 
-def make_workload(name: str, dtype: str, closure: str = "bgk"):
+def make_workload(name: str, dtype: str, closure: str = "bgk", pattern: str = "ab"):
     """Returns (lattice, fields, description) with the lattice initialised.
     closure "mlp" installs seeded random network weights: the cost of the
-    learned closure does not depend on the weight values."""
+    learned closure does not depend on the weight values.  pattern "aa"
+    streams in place in one population array."""
     import numpy as np
     import lbm_inputs as inp
     from paper_2506_09242_gb300 import lbm
@@ -82,7 +83,7 @@ def make_workload(name: str, dtype: str, closure: str = "bgk"):
     if not m:
         raise SystemExit(f"unknown workload {name}")
     kind, n, Q = m.group(1), int(m.group(2)), int(m.group(3))
-    lat = lbm.Lattice(n, n, n, Q, dtype)
+    lat = lbm.Lattice(n, n, n, Q, dtype, pattern=pattern)
     ckind = {"bgk": lbm.CLOSURE_BGK, "smagorinsky": lbm.CLOSURE_SMAGORINSKY, "mlp": lbm.CLOSURE_MLP}[closure]
     if closure == "mlp":
         norm = np.concatenate([np.zeros(6), [1.0], np.full(6, 1e-3), [0.01], [1e-4, 0.0]])
@@ -113,6 +114,9 @@ def make_workload(name: str, dtype: str, closure: str = "bgk"):
                  "fluid_nodes": int(census[lbm.TAG_FLUID] + census[lbm.TAG_FORCED])})
     if closure != "bgk":
         desc["workload"] += f"_{closure}"
+    if pattern != "ab":
+        desc["workload"] += f"_{pattern}"
+        desc["pattern"] = pattern
     return lat, (rho, u), desc
 
 
@@ -369,7 +373,7 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    lat, fields, desc = make_workload(args.workload, args.dtype, args.closure)
+    lat, fields, desc = make_workload(args.workload, args.dtype, args.closure, args.pattern)
     Q = int(desc["lattice"][3:])
     cells = lat.N
     sampler = ClockSampler(local)
@@ -395,15 +399,17 @@ def run_ours(args):
     errors = None
     cpu = None
     if rank == 0 and not args.no_extras:
-        for wl, dt, cl in (("tgv512_d3q19", "f16", "bgk"), ("tgv512_d3q19", "bf16", "bgk"),
-                           ("cavity256_d3q19", "f32", "bgk"), ("tgv512_d3q27", "f32", "bgk"),
-                           ("tgv512_d3q27", "f16", "bgk"), ("tgv512_d3q19", "f32", "smagorinsky"),
-                           ("tgv512_d3q19", "f32", "mlp"), ("tgv128_d3q19", "f32", "bgk"),
-                           ("tgv128_d3q19", "f32", "mlp"), ("porous400_d3q19", "f32", "bgk"),
-                           ("porous400_d3q19", "f16", "bgk")):
-            if (wl, dt, cl) == (args.workload, args.dtype, args.closure):
+        for wl, dt, cl, pat in (("tgv512_d3q19", "f16", "bgk", "ab"), ("tgv512_d3q19", "bf16", "bgk", "ab"),
+                                ("cavity256_d3q19", "f32", "bgk", "ab"), ("tgv512_d3q27", "f32", "bgk", "ab"),
+                                ("tgv512_d3q27", "f16", "bgk", "ab"), ("tgv512_d3q19", "f32", "smagorinsky", "ab"),
+                                ("tgv512_d3q19", "f32", "mlp", "ab"), ("tgv128_d3q19", "f32", "bgk", "ab"),
+                                ("tgv128_d3q19", "f32", "mlp", "ab"), ("porous400_d3q19", "f32", "bgk", "ab"),
+                                ("porous400_d3q19", "f16", "bgk", "ab"), ("tgv512_d3q19", "f32", "bgk", "aa"),
+                                ("tgv512_d3q19", "f16", "bgk", "aa"), ("cavity256_d3q19", "f32", "bgk", "aa"),
+                                ("porous400_d3q19", "f32", "bgk", "aa")):
+            if (wl, dt, cl, pat) == (args.workload, args.dtype, args.closure, args.pattern):
                 continue
-            v, _, d = make_workload(wl, dt, cl)
+            v, _, d = make_workload(wl, dt, cl, pat)
             tms, kms, _ = time_lattice(v, 5, 3, args.inner)
             q = int(d["lattice"][3:])
             ach = 2 * q * SIZE[dt] * v.N / (kms * 1e-3) / 1e9
@@ -458,6 +464,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="tgv512_d3q19")
     ap.add_argument("--dtype", default="f32", choices=sorted(SIZE))
     ap.add_argument("--closure", default="bgk", choices=CLOSURES)
+    ap.add_argument("--pattern", default="ab", choices=("ab", "aa"),
+                    help="streaming pattern: two arrays (ab) or one array updated in place (aa)")
     ap.add_argument("--inner", type=int, default=20, help="lattice steps per benchmark step (>= 2)")
     ap.add_argument("--ref-n", type=int, default=64, help="lattice size of the oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip variants, error table and CPU baseline")

@@ -58,6 +58,17 @@ typedef enum { LBM_D3Q19 = 19, LBM_D3Q27 = 27 } lbm_lattice;
  * The 16-bit types round to nearest-even on store. */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16_SHIFTED = 2, LBM_BF16_SHIFTED = 3 } lbm_dtype;
 
+/* Streaming pattern (Sec. 2.3.1 names both; the paper's port uses the
+ * two-population scheme and leaves the AA pattern to future work).
+ *   LBM_PATTERN_AB: two population arrays; each step pulls from one and
+ *     writes the other.
+ *   LBM_PATTERN_AA: one array updated in place, steps alternating between a
+ *     local step (read and write the node's own slots) and a step that reads
+ *     from and writes to the neighbours; half the population memory, the
+ *     same bytes moved per step and the same results, bit for bit, as AB
+ *     (the arithmetic per node is identical). */
+typedef enum { LBM_PATTERN_AB = 0, LBM_PATTERN_AA = 1 } lbm_pattern;
+
 /* Node tags (Sec. 2.3.2: one integer per node selects the node's model). */
 enum {
     LBM_TAG_FLUID = 0,  /* fluid node, collision only                               */
@@ -131,6 +142,18 @@ typedef struct {
  * stays allocated.  Errors: ARG, OOM, CUDA. */
 lbm_status lbm_create(int nx, int ny, int nz, lbm_lattice lattice, lbm_dtype dtype, const lbm_allocator *alloc,
                       void *stream, lbm_ctx **out);
+
+/* lbm_create with a streaming pattern (lbm_create is LBM_PATTERN_AB).  With
+ * LBM_PATTERN_AA one population array is allocated, and after an odd number
+ * of steps since the last initialisation the state is held in the
+ * neighbour-shifted layout: every call still sees the same state (moments,
+ * reductions and lbm_get_populations read either layout), but lbm_set_tags
+ * then returns LBM_ERR_STATE, since the bounced links are stored according
+ * to the old tags; take one more step first.  The two-nodes-per-thread
+ * kernel of 16-bit storage is A/B only (AA steps use one node per thread).
+ * Errors: as lbm_create, and ARG for an unknown pattern. */
+lbm_status lbm_create_ex(int nx, int ny, int nz, lbm_lattice lattice, lbm_dtype dtype, lbm_pattern pattern,
+                         const lbm_allocator *alloc, void *stream, lbm_ctx **out);
 
 /* Waits for the context's stream and frees everything it owns.  NULL is a
  * no-op. */

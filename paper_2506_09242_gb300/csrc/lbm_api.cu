@@ -39,6 +39,11 @@ struct lbm_ctx {
     long long nfp = 0;
     bool compact_valid = false;  // cA holds the current state
     bool dense_stale = false;    // A lacks the current state (it is in cA)
+    // AA pattern: one array (B and cB stay NULL), updated in place; aa_p is
+    // set while the state is in layout P (after an odd step; the next step
+    // is an even one).
+    bool aa = false;
+    bool aa_p = false;
     // CUDA graphs of two steps (X -> Y, Y -> X), replayed on a private stream
     // ordered after / before the caller's stream by events.  One graph per
     // kernel path (dense, compact) and array orientation; any change of
@@ -129,7 +134,7 @@ Launch make_launch(lbm_ctx *ctx)
     L.Q = ctx->Q;
     L.g = ctx->g;
     L.A = ctx->A;
-    L.B = ctx->B;
+    L.B = ctx->aa ? ctx->A : ctx->B;
     L.tags = ctx->tags;
     L.general = ctx->general;
     L.closure = ctx->params.closure;
@@ -137,6 +142,8 @@ Launch make_launch(lbm_ctx *ctx)
     L.fluid_mask = ctx->fluid_mask;
     L.n_list = ctx->n_list;
     L.stream = ctx->stream;
+    L.aa = ctx->aa;
+    L.aa_p = ctx->aa_p;
     return L;
 }
 
@@ -361,10 +368,11 @@ static lbm_status build_fluid_list(lbm_ctx *ctx, bool wanted)
     ctx->nfp = (total + 255) / 256 * 256;
     const size_t cbytes = (size_t)ctx->Q * ctx->nfp * ctx->elem;
     ctx->cA = dev_alloc(ctx, cbytes);
-    ctx->cB = dev_alloc(ctx, cbytes);
+    ctx->cB = ctx->aa ? nullptr : dev_alloc(ctx, cbytes);
     ctx->nbr = (int *)dev_alloc(ctx, sizeof(int) * (size_t)(ctx->Q - 1) * ctx->nfp);
     Tmp index(ctx, sizeof(int) * (size_t)ctx->g.sN);
-    if (!ctx->cA || !ctx->cB || !ctx->nbr || !index.p) return fail(ctx, LBM_ERR_OOM, "compact storage allocation failed");
+    if (!ctx->cA || (!ctx->aa && !ctx->cB) || !ctx->nbr || !index.p)
+        return fail(ctx, LBM_ERR_OOM, "compact storage allocation failed");
     CUDA_TRY(ctx, launch_build_neighbours(ctx->Q, ctx->g, ctx->tags, ctx->fluid_list, total, ctx->nfp, (int *)index.p,
                                           ctx->nbr, ctx->stream),
              "neighbour index");
@@ -455,8 +463,16 @@ lbm_status lbm_destroy(lbm_ctx *ctx)
 lbm_status lbm_create(int nx, int ny, int nz, lbm_lattice lattice, lbm_dtype dtype, const lbm_allocator *alloc,
                       void *stream, lbm_ctx **out)
 {
+    return lbm_create_ex(nx, ny, nz, lattice, dtype, LBM_PATTERN_AB, alloc, stream, out);
+}
+
+lbm_status lbm_create_ex(int nx, int ny, int nz, lbm_lattice lattice, lbm_dtype dtype, lbm_pattern pattern,
+                         const lbm_allocator *alloc, void *stream, lbm_ctx **out)
+{
     if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
+    if (pattern != LBM_PATTERN_AB && pattern != LBM_PATTERN_AA)
+        return fail(nullptr, LBM_ERR_ARG, "unknown streaming pattern %d", (int)pattern);
     if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_ERR_ARG, "lattice sizes must be >= 1");
     if (lattice != LBM_D3Q19 && lattice != LBM_D3Q27) return fail(nullptr, LBM_ERR_ARG, "unknown lattice %d", (int)lattice);
     if (dtype < LBM_F64 || dtype > LBM_BF16_SHIFTED) return fail(nullptr, LBM_ERR_ARG, "unknown dtype %d", (int)dtype);
@@ -474,6 +490,7 @@ lbm_status lbm_create(int nx, int ny, int nz, lbm_lattice lattice, lbm_dtype dty
     ctx->px = (int)px;
     ctx->Q = (int)lattice;
     ctx->dtype = dtype;
+    ctx->aa = pattern == LBM_PATTERN_AA;
     ctx->elem = dtype == LBM_F64 ? 8 : dtype == LBM_F32 ? 4 : 2;
     ctx->g.nx = nx;
     ctx->g.ny = ny;
@@ -493,19 +510,19 @@ lbm_status lbm_create(int nx, int ny, int nz, lbm_lattice lattice, lbm_dtype dty
     ctx->params.trt_magic = 3.0 / 16.0;
 
     ctx->A = dev_alloc(ctx, ctx->pop_bytes);
-    ctx->B = dev_alloc(ctx, ctx->pop_bytes);
+    ctx->B = ctx->aa ? nullptr : dev_alloc(ctx, ctx->pop_bytes);
     ctx->tags = (uint8_t *)dev_alloc(ctx, (size_t)ctx->g.sN);
     ctx->partials = (double *)dev_alloc(ctx, sizeof(double) * kRedBlocks * kRedSlots);
     ctx->red_out = (double *)dev_alloc(ctx, sizeof(double) * kRedSlots);
     ctx->census_dev = (unsigned long long *)dev_alloc(ctx, sizeof(unsigned long long) * (LBM_NTAGS + 1));
-    if (!ctx->A || !ctx->B || !ctx->tags || !ctx->partials || !ctx->red_out || !ctx->census_dev) {
+    if (!ctx->A || (!ctx->aa && !ctx->B) || !ctx->tags || !ctx->partials || !ctx->red_out || !ctx->census_dev) {
+        const double gb = ((ctx->aa ? 1.0 : 2.0) * ctx->pop_bytes + ctx->g.sN) / 1e9;
         lbm_destroy(ctx);
-        return fail(nullptr, LBM_ERR_OOM, "device allocation of %.3f GB failed",
-                    (2.0 * ctx->pop_bytes + ctx->g.sN) / 1e9);
+        return fail(nullptr, LBM_ERR_OOM, "device allocation of %.3f GB failed", gb);
     }
     cudaError_t e = cudaMemsetAsync(ctx->tags, 0, (size_t)ctx->g.sN, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->A, 0, ctx->pop_bytes, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->B, 0, ctx->pop_bytes, ctx->stream);
+    if (e == cudaSuccess && ctx->B) e = cudaMemsetAsync(ctx->B, 0, ctx->pop_bytes, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         lbm_destroy(ctx);
@@ -529,6 +546,10 @@ lbm_status lbm_set_params(lbm_ctx *ctx, const lbm_params *p)
 lbm_status lbm_set_tags(lbm_ctx *ctx, const uint8_t *tags, int on_device)
 {
     if (!ctx || !tags) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    if (ctx->aa && ctx->aa_p)
+        return fail(ctx, LBM_ERR_STATE,
+                    "AA state after an odd number of steps holds bounced links for the current tags: step once more "
+                    "before changing them");
     ENSURE_DENSE(ctx);
     const size_t n = (size_t)ctx->g.N;
     Tmp user(ctx, n);
@@ -606,15 +627,18 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u
         s = sync(ctx);
     }
     ctx->steps = 0;
+    ctx->aa_p = false;
     dense_written(ctx);
     return s;
 }
 
-// One collide-and-stream launch of the current path from X to Y on stream st.
-static cudaError_t launch_one(lbm_ctx *ctx, bool compact, const void *X, void *Y, cudaStream_t st)
+// One collide-and-stream launch of the current path from X to Y on stream st
+// (AA: X == Y, an even step when layout_p, else an odd one).
+static cudaError_t launch_one(lbm_ctx *ctx, bool compact, const void *X, void *Y, cudaStream_t st, bool layout_p)
 {
     Launch L = make_launch(ctx);
     L.stream = st;
+    L.aa_p = ctx->aa && layout_p;
     if (compact)
         return by_dtype(ctx->dtype, [&](auto *tag) {
             using S = std::remove_pointer_t<decltype(tag)>;
@@ -661,8 +685,9 @@ static cudaGraphExec_t two_step_graph(lbm_ctx *ctx, bool compact, const void *X,
         ctx->use_graphs = false;
         return nullptr;
     }
-    const cudaError_t e1 = launch_one(ctx, compact, X, Y, ctx->gstream);
-    const cudaError_t e2 = launch_one(ctx, compact, Y, (void *)X, ctx->gstream);
+    // AB: X -> Y -> X; AA (X == Y): an odd step, then an even one
+    const cudaError_t e1 = launch_one(ctx, compact, X, Y, ctx->gstream, false);
+    const cudaError_t e2 = launch_one(ctx, compact, Y, (void *)X, ctx->gstream, ctx->aa);
     const cudaError_t e3 = cudaStreamEndCapture(ctx->gstream, &graph);
     cudaGraphExec_t exec = nullptr;
     if (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && graph &&
@@ -684,6 +709,36 @@ static cudaGraphExec_t two_step_graph(lbm_ctx *ctx, bool compact, const void *X,
 // large enough and graphs are enabled), the remainder as plain launches.
 static lbm_status run_steps(lbm_ctx *ctx, int n, bool compact)
 {
+    if (ctx->aa) {
+        // In place: an even step first when the state is in layout P, then
+        // (odd, even) pairs, then a final odd step if one is left.
+        void *F = compact ? ctx->cA : ctx->A;
+        if (ctx->aa_p && n > 0) {
+            CUDA_TRY(ctx, launch_one(ctx, compact, F, F, ctx->stream, true), "collide-stream launch");
+            ctx->aa_p = false;
+            ++ctx->steps;
+            --n;
+        }
+        const int pairs = (ctx->use_graphs && n >= 4) ? n / 2 : 0;
+        if (pairs) {
+            cudaGraphExec_t exec = two_step_graph(ctx, compact, F, F);
+            if (exec) {
+                CUDA_TRY(ctx, cudaEventRecord(ctx->ev_in, ctx->stream), "graph order");
+                CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev_in, 0), "graph order");
+                for (int r = 0; r < pairs; ++r) CUDA_TRY(ctx, cudaGraphLaunch(exec, ctx->gstream), "graph launch");
+                CUDA_TRY(ctx, cudaEventRecord(ctx->ev_out, ctx->gstream), "graph order");
+                CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_out, 0), "graph order");
+                ctx->steps += 2LL * pairs;
+                n -= 2 * pairs;
+            }
+        }
+        for (int k = 0; k < n; ++k) {
+            CUDA_TRY(ctx, launch_one(ctx, compact, F, F, ctx->stream, ctx->aa_p), "collide-stream launch");
+            ctx->aa_p = !ctx->aa_p;
+            ++ctx->steps;
+        }
+        return LBM_OK;
+    }
     void **X = compact ? &ctx->cA : &ctx->A;
     void **Y = compact ? &ctx->cB : &ctx->B;
     int pairs = (ctx->use_graphs && n >= 4) ? n / 2 : 0;
@@ -700,7 +755,7 @@ static lbm_status run_steps(lbm_ctx *ctx, int n, bool compact)
         }
     }
     for (int k = 0; k < n; ++k) {
-        CUDA_TRY(ctx, launch_one(ctx, compact, *X, *Y, ctx->stream), "collide-stream launch");
+        CUDA_TRY(ctx, launch_one(ctx, compact, *X, *Y, ctx->stream, false), "collide-stream launch");
         std::swap(*X, *Y);
         ++ctx->steps;
     }
@@ -757,7 +812,10 @@ lbm_status lbm_step_reduce(lbm_ctx *ctx, int n, lbm_reduction *out)
                  return launch_step_reduce<S>(L, ctx->params, ctx->fpart);
              }),
              "fused collide-stream-reduce launch");
-    std::swap(ctx->A, ctx->B);
+    if (ctx->aa)
+        ctx->aa_p = !ctx->aa_p;
+    else
+        std::swap(ctx->A, ctx->B);
     ++ctx->steps;
     CUDA_TRY(ctx, launch_reduce_partials(ctx->fpart, nparts, ctx->partials, ctx->red_out, ctx->stream), "reduce");
     double r[kRedSlots];
@@ -861,6 +919,7 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device)
 {
     if (!ctx || !f) return fail(ctx, LBM_ERR_ARG, "NULL argument");
     dense_written(ctx);
+    ctx->aa_p = false;  // AA: written in layout S
     const size_t nb = sizeof(double) * (size_t)ctx->g.N;
     Tmp plane(ctx, on_device ? 0 : nb);
     if (!on_device && !plane.p) return fail(ctx, LBM_ERR_OOM, "staging allocation failed");

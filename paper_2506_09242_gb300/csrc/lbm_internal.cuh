@@ -49,11 +49,14 @@ __host__ __device__ constexpr T wgt(int Q, int i)
 
 // ---------------------------------------------------------------------------
 // Storage traits: load h = f - w into the compute type, store rounded.
+// ld goes through the read-only data path (arrays a kernel only reads); ldc
+// is a plain coherent load, for arrays the kernel also writes.
 // ---------------------------------------------------------------------------
 template <typename S> struct Store;
 template <> struct Store<double> {
     using T = double;
     static __device__ __forceinline__ T ld(const double *p) { return __ldg(p); }
+    static __device__ __forceinline__ T ldc(const double *p) { return *p; }
     static __device__ __forceinline__ void st(double *p, T v) { *p = v; }
     static __device__ __forceinline__ double from_f64(double v) { return v; }
     static __device__ __forceinline__ T rt(T v) { return v; }  // value as stored
@@ -61,6 +64,7 @@ template <> struct Store<double> {
 template <> struct Store<float> {
     using T = float;
     static __device__ __forceinline__ T ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ T ldc(const float *p) { return *p; }
     static __device__ __forceinline__ void st(float *p, T v) { *p = v; }
     static __device__ __forceinline__ float from_f64(double v) { return (float)v; }
     static __device__ __forceinline__ T rt(T v) { return v; }
@@ -68,6 +72,7 @@ template <> struct Store<float> {
 template <> struct Store<__half> {
     using T = float;
     static __device__ __forceinline__ T ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ T ldc(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half *p, T v) { *p = __float2half_rn(v); }
     static __device__ __forceinline__ __half from_f64(double v) { return __float2half_rn((float)v); }
     static __device__ __forceinline__ T rt(T v) { return __half2float(__float2half_rn(v)); }
@@ -75,6 +80,7 @@ template <> struct Store<__half> {
 template <> struct Store<__nv_bfloat16> {
     using T = float;
     static __device__ __forceinline__ T ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ T ldc(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, T v) { *p = __float2bfloat16_rn(v); }
     static __device__ __forceinline__ __nv_bfloat16 from_f64(double v) { return __float2bfloat16_rn((float)v); }
     static __device__ __forceinline__ T rt(T v) { return __bfloat162float(__float2bfloat16_rn(v)); }
@@ -133,9 +139,13 @@ struct Launch {
     const uint32_t *fluid_mask;  // per listed fluid node: kListForced (compact step)
     long long n_list;            // number of listed fluid nodes
     cudaStream_t stream;
+    bool aa = false;    // AA pattern: one array, A == B
+    bool aa_p = false;  // AA state in layout P (the next step is an even one)
 };
 
-// Per-storage-type launchers (one translation unit per type).
+// Per-storage-type launchers (one translation unit per type; each entry
+// point hands AA launches (L.aa) to its _aa counterpart, which lives in the
+// type's AA translation unit).
 template <typename S> cudaError_t launch_step(const Launch &L, const lbm_params &p);
 // One step that also writes per-block FP32 reduction partials of the new
 // state, kRedSlots floats per block (cudaErrorNotSupported for FP64 storage
@@ -151,6 +161,15 @@ cudaError_t launch_moments(const Launch &L, const lbm_params &p, double *rho, do
 template <typename S>
 cudaError_t launch_init(const Launch &L, const double *rho, const double *u);
 template <typename S> cudaError_t launch_get_pop(const Launch &L, int i, double *f_plane);
+template <typename S> cudaError_t launch_step_aa(const Launch &L, const lbm_params &p);
+template <typename S> cudaError_t launch_step_reduce_aa(const Launch &L, const lbm_params &p, float *partials);
+template <typename S>
+cudaError_t launch_step_compact_aa(const Launch &L, const lbm_params &p, const void *Ac, void *Bc, const int *nbr,
+                                   long long nfp);
+template <typename S>
+cudaError_t launch_reduce_aa(const Launch &L, const lbm_params &p, double *partials, int nblocks, double *out);
+template <typename S> cudaError_t launch_moments_aa(const Launch &L, const lbm_params &p, double *rho, double *u);
+template <typename S> cudaError_t launch_get_pop_aa(const Launch &L, int i, double *f_plane);
 template <typename S> cudaError_t launch_set_pop(const Launch &L, int i, const double *f_plane);
 
 // Storage-type independent kernels (lbm_api.cu).

@@ -55,7 +55,63 @@ struct Nbr {
     {
         return row[1 - cvel(i, 1)][1 - cvel(i, 2)] + xs[1 - cvel(i, 0)];
     }
+    // Offset of the node x + c_i (where direction i streams to).
+    __device__ __forceinline__ int dst(int i) const { return src(opp(i)); }
 };
+
+// ---------------------------------------------------------------------------
+// Streaming patterns.  AB (two arrays): a step pulls from A and writes B at
+// the node.  AA (one array F, updated in place; Bailey et al. 2009): steps
+// alternate between
+//   odd:  h_i = F[opp(i)][x - c_i]  and  f*_i -> F[i][x + c_i],
+//   even: h_i = F[i][x]             and  f*_i -> F[opp(i)][x],
+// so within a step every location is read and then written by one thread
+// only.  Between steps F holds the state f*(x) in one of two layouts:
+//   S (after initialisation, set_populations and even steps):
+//       F[opp(i)][x] = f*_i(x);
+//   P (after odd steps): F[i][x + c_i] = f*_i(x), except where x + c_i is a
+//       SOLID or WALL node: there the link's bounce-back is kept in place,
+//       F[opp(i)][x] = f*_i(x), and the next even step adds the moving-wall
+//       term to it.
+// In both layouts F[.][x] belongs to node x alone, so node-by-node copies
+// (the compact fluid-only hand-over) keep the layout.
+// ---------------------------------------------------------------------------
+enum : int { kPatAB = 0, kPatAAOdd = 1, kPatAAEven = 2 };
+enum : int { kLayAB = 0, kLayS = 1, kLayP = 2 };
+
+// Step pattern / read layout of a launch.
+inline int step_pattern(bool aa, bool layout_p) { return !aa ? kPatAB : layout_p ? kPatAAEven : kPatAAOdd; }
+inline int read_layout(bool aa, bool layout_p) { return !aa ? kLayAB : layout_p ? kLayP : kLayS; }
+
+// A population load of a step: the read-only path for AB (A is never
+// written by the launch), a coherent load for AA, where the same thread
+// later writes the location (through the same pointer).
+template <typename S, int PAT> __device__ __forceinline__ typename Store<S>::T pop_ld(const S *p)
+{
+    if constexpr (PAT == kPatAB)
+        return Store<S>::ld(p);
+    else
+        return Store<S>::ldc(p);
+}
+
+// Offset of the value a step reads for direction i from a non-wall source.
+template <int PAT>
+__device__ __forceinline__ long long step_load_off(int i, const Grid &g, const Nbr &nb)
+{
+    if (PAT == kPatAB) return (long long)i * g.sN + nb.src(i);
+    if (PAT == kPatAAOdd) return (long long)opp(i) * g.sN + nb.src(i);
+    return (long long)i * g.sN + nb.self;
+}
+
+// Offset a step writes f*_i to; wall: bit j set when the source of direction
+// j is a SOLID or WALL node (only the odd AA step looks at it).
+template <int PAT>
+__device__ __forceinline__ long long step_store_off(int i, const Grid &g, const Nbr &nb, uint32_t wall)
+{
+    if (PAT == kPatAB) return (long long)i * g.sN + nb.self;
+    if (PAT == kPatAAEven) return (long long)opp(i) * g.sN + nb.self;
+    return ((wall >> opp(i)) & 1u) ? (long long)opp(i) * g.sN + nb.self : (long long)i * g.sN + nb.dst(i);
+}
 
 // ---------------------------------------------------------------------------
 // Reduction helpers (FP64 sums over fluid nodes).
@@ -261,18 +317,26 @@ __device__ __forceinline__ long long linear_block() { return blockIdx.x + (long 
 // Boundary rules for one fluid node next to a wall (tag bit kNearWall):
 // halfway bounce-back from a SOLID source, h_i(x) = h*_opp(i)(x); Ladd's
 // moving-wall term from a WALL_k source, + 6 w_i rho_wall (c_i . u_wall_k).
+// Where the bounced value sits depends on the pattern: AB reads it from
+// A[opp(i)][x], the odd AA step from F[i][x] (layout S), and the even AA step
+// has already read it from F[i][x] (layout P) and only adds the wall term.
+// Returns the links with a SOLID or WALL source (bit i).
 // ---------------------------------------------------------------------------
-template <int Q, typename S>
-__device__ __forceinline__ void apply_walls(typename Store<S>::T (&h)[Q], const S *__restrict__ A,
-                                            const uint8_t *__restrict__ tags, const Grid &g, const Nbr &nb,
-                                            const KParams<typename Store<S>::T> &p)
+template <int Q, typename S, int PAT = kPatAB>
+__device__ __forceinline__ uint32_t apply_walls(typename Store<S>::T (&h)[Q], const S *__restrict__ A,
+                                                const uint8_t *__restrict__ tags, const Grid &g, const Nbr &nb,
+                                                const KParams<typename Store<S>::T> &p)
 {
     using T = typename Store<S>::T;
+    uint32_t wall = 0;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const unsigned ts = tags[nb.src(i)] & kTagMask;
         if (is_wall_tag(ts)) {
-            T v = Store<S>::ld(A + (long long)opp(i) * g.sN + nb.self);
+            wall |= 1u << i;
+            T v = PAT == kPatAB      ? pop_ld<S, PAT>(A + (long long)opp(i) * g.sN + nb.self)
+                  : PAT == kPatAAOdd ? pop_ld<S, PAT>(A + (long long)i * g.sN + nb.self)
+                                     : h[i];
             if (ts >= LBM_TAG_WALL0) {
                 // select the wall's velocity without indexing the parameter
                 // block dynamically (which would copy it to local memory)
@@ -289,6 +353,7 @@ __device__ __forceinline__ void apply_walls(typename Store<S>::T (&h)[Q], const 
             h[i] = v;
         }
     }
+    return wall;
 }
 
 // ---------------------------------------------------------------------------
@@ -449,7 +514,7 @@ __device__ __forceinline__ Macro<T> collide_node(T (&h)[Q], bool forced, const K
 // collision used where the storage is FP32 (mass and momentum are collision
 // invariants), otherwise recomputed from the post-collision set rounded to
 // the storage type, which is what a later pass over memory would read.
-template <int Q, typename S, bool GENERAL, int CLOSURE, bool REDUCE>
+template <int Q, typename S, bool GENERAL, int CLOSURE, bool REDUCE, int PAT>
 __device__ __forceinline__ void collide_stream_node(const S *__restrict__ A, S *__restrict__ B,
                                                     const uint8_t *__restrict__ tags, const Grid &g,
                                                     const KParams<typename Store<S>::T> &p, int x, int y, int z,
@@ -465,11 +530,14 @@ __device__ __forceinline__ void collide_stream_node(const S *__restrict__ A, S *
         if (is_wall_tag(t & kTagMask)) return;
     }
 
-    // Pull: h_i(x) = h*_i(x - c_i).
+    // Pull: h_i(x) = h*_i(x - c_i).  AA reads through B, the pointer the
+    // launch writes, so same-address loads and stores keep program order.
+    const S *F = PAT == kPatAB ? A : B;
     T h[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) h[i] = St::ld(A + (long long)i * g.sN + nb.src(i));
-    if (GENERAL && (t & kNearWall)) apply_walls<Q, S>(h, A, tags, g, nb, p);
+    for (int i = 0; i < Q; ++i) h[i] = pop_ld<S, PAT>(F + step_load_off<PAT>(i, g, nb));
+    uint32_t wall = 0;
+    if (GENERAL && (t & kNearWall)) wall = apply_walls<Q, S, PAT>(h, F, tags, g, nb, p);
 
     const bool forced = GENERAL && (t & kTagMask) == LBM_TAG_FORCED;
     const Macro<T> m = collide_node<Q, T, CLOSURE>(h, forced, p);
@@ -486,16 +554,18 @@ __device__ __forceinline__ void collide_stream_node(const S *__restrict__ A, S *
     }
 
 #pragma unroll
-    for (int i = 0; i < Q; ++i) St::st(B + (long long)i * g.sN + nb.self, h[i]);
+    for (int i = 0; i < Q; ++i) St::st(B + step_store_off<PAT>(i, g, nb, wall), h[i]);
 }
 
-// Fused collide-and-stream (pull, two populations), one node per thread.
+// Fused collide-and-stream, one node per thread.
 //   GENERAL: tags are read (bounce-back, Ladd walls, forced nodes); without
 //            it every node is a plain fluid node and no tag byte is touched.
 //   CLOSURE: LBM_CLOSURE_BGK, _SMAGORINSKY, _STREAM_ONLY or _TRT.
 //   REDUCE:  also writes this block's reduction partial of the new state to
 //            partials[linear block index][0..kRedSlots).
-template <int Q, typename S, bool GENERAL, int CLOSURE, bool REDUCE>
+//   PAT:     kPatAB (A -> B), or an odd or even AA step, in place in B (A is
+//            not accessed; no location is touched by two threads).
+template <int Q, typename S, bool GENERAL, int CLOSURE, bool REDUCE, int PAT = kPatAB>
 __global__ void __launch_bounds__(kStepThreads)
     k_collide_stream(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ tags, Grid g,
                      KParams<typename Store<S>::T> p, float *__restrict__ partials)
@@ -504,7 +574,8 @@ __global__ void __launch_bounds__(kStepThreads)
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     NodeSums ns;
-    if (x < g.nx && y < g.ny) collide_stream_node<Q, S, GENERAL, CLOSURE, REDUCE>(A, B, tags, g, p, x, y, z, ns);
+    if (x < g.nx && y < g.ny)
+        collide_stream_node<Q, S, GENERAL, CLOSURE, REDUCE, PAT>(A, B, tags, g, p, x, y, z, ns);
     if constexpr (REDUCE) block_partial_f32(ns, partials + linear_block() * kRedSlots);
 }
 
@@ -533,7 +604,7 @@ __device__ __forceinline__ T wall_term(int i, unsigned ts, const KParams<T> &p)
 // same single load as a streamed one.  (The learned closure needs whole warps
 // of consecutive nodes and keeps the dense sweep.)
 // ---------------------------------------------------------------------------
-template <int Q, typename S, int CLOSURE>
+template <int Q, typename S, int CLOSURE, int PAT = kPatAB>
 __global__ void __launch_bounds__(kStepThreads)
     k_collide_stream_compact(const S *__restrict__ A, S *__restrict__ B, const int *__restrict__ nbr,
                              const uint32_t *__restrict__ mask, long long n, long long nfp,
@@ -543,19 +614,55 @@ __global__ void __launch_bounds__(kStepThreads)
     using St = Store<S>;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= n) return;
+    const S *F = PAT == kPatAB ? A : B;  // AA: in place through B
+    const uint32_t m = __ldg(mask + t);
     T h[Q];
-    h[0] = St::ld(A + t);
+    if constexpr (PAT == kPatAAEven) {
+        // Local reads (layout P); links from a moving wall add Ladd's term.
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const int s = __ldg(nbr + (long long)(i - 1) * nfp + t);
-        const long long a = s >= 0 ? (long long)i * nfp + s : (long long)opp(i) * nfp + t;
-        T v = St::ld(A + a);
-        if (s < -1) v += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - s), p);
-        h[i] = v;
+        for (int i = 0; i < Q; ++i) h[i] = St::ldc(F + (long long)i * nfp + t);
+        if (m & kListAnyWall) {
+#pragma unroll
+            for (int i = 1; i < Q; ++i)
+                if ((m >> i) & 1u) {
+                    const int s = __ldg(nbr + (long long)(i - 1) * nfp + t);
+                    if (s < -1) h[i] += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - s), p);
+                }
+        }
+        collide_node<Q, T, CLOSURE>(h, (m & kListForced) != 0u, p);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) St::st(B + (long long)opp(i) * nfp + t, h[i]);
+    } else {
+        // AB: h_i = A[i][s_i]; odd AA: h_i = F[opp(i)][s_i] and f*_i goes to
+        // F[i][s_opp(i)], the list position of x + c_i.  A bounced link reads
+        // (and, in AA, writes back) the node's own slot.
+        int sv[Q];
+        sv[0] = 0;
+        h[0] = pop_ld<S, PAT>(F + t);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const int s = __ldg(nbr + (long long)(i - 1) * nfp + t);
+            sv[i] = s;
+            const int slot = PAT == kPatAB ? i : opp(i);
+            const long long a = s >= 0 ? (long long)slot * nfp + s
+                                       : (long long)(PAT == kPatAB ? opp(i) : i) * nfp + t;
+            T v = pop_ld<S, PAT>(F + a);
+            if (s < -1) v += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - s), p);
+            h[i] = v;
+        }
+        collide_node<Q, T, CLOSURE>(h, (m & kListForced) != 0u, p);
+        if constexpr (PAT == kPatAB) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) St::st(B + (long long)i * nfp + t, h[i]);
+        } else {
+            St::st(B + t, h[0]);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const int d = sv[opp(i)];
+                St::st(B + (d >= 0 ? (long long)i * nfp + d : (long long)opp(i) * nfp + t), h[i]);
+            }
+        }
     }
-    collide_node<Q, T, CLOSURE>(h, (__ldg(mask + t) & kListForced) != 0u, p);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) St::st(B + (long long)i * nfp + t, h[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -565,7 +672,7 @@ __global__ void __launch_bounds__(kStepThreads)
 // network, so lanes past the row end and solid nodes only skip their loads
 // and stores.  Requires blockDim.x to be a multiple of 32.
 // ---------------------------------------------------------------------------
-template <int Q, typename S, bool GENERAL>
+template <int Q, typename S, bool GENERAL, int PAT = kPatAB>
 __global__ void __launch_bounds__(kStepThreads)
     k_collide_stream_mlp(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ tags, Grid g,
                          KParams<typename Store<S>::T> p, const MlpSmem *__restrict__ mlp_image)
@@ -591,10 +698,12 @@ __global__ void __launch_bounds__(kStepThreads)
         t = tags[nb.self];
         active = !is_wall_tag(t & kTagMask);
     }
+    const S *F = PAT == kPatAB ? A : B;  // AA: in place through B
     T h[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) h[i] = active ? St::ld(A + (long long)i * g.sN + nb.src(i)) : T(0);
-    if (GENERAL && active && (t & kNearWall)) apply_walls<Q, S>(h, A, tags, g, nb, p);
+    for (int i = 0; i < Q; ++i) h[i] = active ? pop_ld<S, PAT>(F + step_load_off<PAT>(i, g, nb)) : T(0);
+    uint32_t wall = 0;
+    if (GENERAL && active && (t & kNearWall)) wall = apply_walls<Q, S, PAT>(h, F, tags, g, nb, p);
 
     const bool forced = GENERAL && (t & kTagMask) == LBM_TAG_FORCED;
     const Macro<T> m = node_macros<Q, T>(h, forced, p);
@@ -606,7 +715,7 @@ __global__ void __launch_bounds__(kStepThreads)
     relax<Q, T>(h, m, T(1) / (p.tau + T(dtau)), forced);
     if (active) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) St::st(B + (long long)i * g.sN + nb.self, h[i]);
+        for (int i = 0; i < Q; ++i) St::st(B + step_store_off<PAT>(i, g, nb, wall), h[i]);
     }
 }
 
@@ -787,8 +896,22 @@ __global__ void __launch_bounds__(kStepThreads)
 // ---------------------------------------------------------------------------
 // Per-node density and velocity from the stored post-collision set.
 // ---------------------------------------------------------------------------
-template <int Q, typename S>
-__device__ __forceinline__ void node_moments(const S *__restrict__ A, long long sN, int off, bool forced,
+// Offset of f*_i(x) in read layout LAY (AB, AA layout S or P).  Layout P
+// looks at x + c_i: nb must be initialised and near_wall = the node's
+// kNearWall bit; AB and S use nb.self only.
+template <int LAY>
+__device__ __forceinline__ long long fstar_off(int i, const Grid &g, const Nbr &nb, bool near_wall,
+                                               const uint8_t *__restrict__ tags)
+{
+    if (LAY == kLayAB) return (long long)i * g.sN + nb.self;
+    if (LAY == kLayS) return (long long)opp(i) * g.sN + nb.self;
+    if (i != 0 && near_wall && is_wall_tag(tags[nb.dst(i)] & kTagMask)) return (long long)opp(i) * g.sN + nb.self;
+    return (long long)i * g.sN + nb.dst(i);
+}
+
+template <int Q, typename S, int LAY>
+__device__ __forceinline__ void node_moments(const S *__restrict__ A, const Grid &g, const Nbr &nb, bool near_wall,
+                                             const uint8_t *__restrict__ tags, bool forced,
                                              const KParams<typename Store<S>::T> &p, typename Store<S>::T &drho,
                                              typename Store<S>::T (&u)[3])
 {
@@ -796,7 +919,7 @@ __device__ __forceinline__ void node_moments(const S *__restrict__ A, long long 
     T d = T(0), jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const T v = Store<S>::ld(A + (long long)i * sN + off);
+        const T v = Store<S>::ld(A + fstar_off<LAY>(i, g, nb, near_wall, tags));
         d += v;
         if (cvel(i, 0)) jx += cvel(i, 0) > 0 ? v : -v;
         if (cvel(i, 1)) jy += cvel(i, 1) > 0 ? v : -v;
@@ -815,7 +938,17 @@ __device__ __forceinline__ void node_moments(const S *__restrict__ A, long long 
     u[2] = jz * inv;
 }
 
-template <int Q, typename S, bool GENERAL>
+// The node (x, y, z) for a read in layout LAY: the full neighbourhood for
+// layout P, the node's own offset otherwise.
+template <int LAY> __device__ __forceinline__ void read_node(Nbr &nb, const Grid &g, int x, int y, int z)
+{
+    if (LAY == kLayP)
+        nb.init(g, x, y, z);
+    else
+        nb.self = (z * g.ny + y) * g.px + x;
+}
+
+template <int Q, typename S, bool GENERAL, int LAY = kLayAB>
 __global__ void __launch_bounds__(kStepThreads)
     k_moments(const S *__restrict__ A, const uint8_t *__restrict__ tags, Grid g, KParams<typename Store<S>::T> p,
               double *__restrict__ rho, double *__restrict__ u)
@@ -825,16 +958,18 @@ __global__ void __launch_bounds__(kStepThreads)
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const int off = (z * g.ny + y) * g.px + x;
+    Nbr nb;
+    read_node<LAY>(nb, g, x, y, z);
     const long long n = x + (long long)g.nx * (y + (long long)g.ny * z);
-    unsigned t = GENERAL ? (tags[off] & kTagMask) : 0u;
+    const unsigned tb = GENERAL ? tags[nb.self] : 0u;
+    const unsigned t = tb & kTagMask;
     if (is_wall_tag(t)) {
         if (rho) rho[n] = 0.0;
         if (u) u[n] = u[g.N + n] = u[2 * g.N + n] = 0.0;
         return;
     }
     T d, v[3];
-    node_moments<Q, S>(A, g.sN, off, t == LBM_TAG_FORCED, p, d, v);
+    node_moments<Q, S, LAY>(A, g, nb, (tb & kNearWall) != 0u, tags, t == LBM_TAG_FORCED, p, d, v);
     if (rho) rho[n] = 1.0 + (double)d;
     if (u) {
         u[n] = (double)v[0];
@@ -849,7 +984,7 @@ __global__ void __launch_bounds__(kStepThreads)
 // range of the padded node index, its threads side by side), pass 2 adds the
 // partials in a fixed order, so the result does not depend on scheduling.
 // ---------------------------------------------------------------------------
-template <int Q, typename S, bool GENERAL>
+template <int Q, typename S, bool GENERAL, int LAY = kLayAB>
 __global__ void __launch_bounds__(kRedThreads)
     k_reduce(const S *__restrict__ A, const uint8_t *__restrict__ tags, Grid g, KParams<typename Store<S>::T> p,
              double *__restrict__ partials)
@@ -865,10 +1000,18 @@ __global__ void __launch_bounds__(kRedThreads)
         int x = idx % g.px;
         for (; idx < hi; idx += blockDim.x) {
             if (x < g.nx) {
-                const unsigned t = GENERAL ? (tags[idx] & kTagMask) : 0u;
+                const unsigned tb = GENERAL ? tags[idx] : 0u;
+                const unsigned t = tb & kTagMask;
                 if (!is_wall_tag(t)) {
+                    Nbr nb;
+                    if (LAY == kLayP) {
+                        const int row = idx / g.px;
+                        nb.init(g, x, row % g.ny, row / g.ny);
+                    } else {
+                        nb.self = idx;
+                    }
                     T d, v[3];
-                    node_moments<Q, S>(A, g.sN, idx, t == LBM_TAG_FORCED, p, d, v);
+                    node_moments<Q, S, LAY>(A, g, nb, (tb & kNearWall) != 0u, tags, t == LBM_TAG_FORCED, p, d, v);
                     ra.add(d, v);
                 }
             }
@@ -891,9 +1034,11 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_final(const double *__re
 // ---------------------------------------------------------------------------
 // Initialisation and population transfer.
 // ---------------------------------------------------------------------------
+// With aa, one array in layout S (slot opp(i) of the node); B is unused.
 template <int Q, typename S>
 __global__ void __launch_bounds__(kStepThreads)
-    k_init(S *__restrict__ A, S *__restrict__ B, Grid g, const double *__restrict__ rho, const double *__restrict__ u)
+    k_init(S *__restrict__ A, S *__restrict__ B, Grid g, const double *__restrict__ rho, const double *__restrict__ u,
+           bool aa)
 {
     // h_eq in the compute type (FP32 except for FP64 storage).
     using T = typename Store<S>::T;
@@ -913,29 +1058,40 @@ __global__ void __launch_bounds__(kStepThreads)
         const T heq = wgt<T>(Q, i) * (dr + r * (cu * (T(3) + T(4.5) * cu) - usq15));
         S v;
         Store<S>::st(&v, heq);
-        A[(long long)i * g.sN + off] = v;
-        B[(long long)i * g.sN + off] = v;
+        if (aa) {
+            A[(long long)opp(i) * g.sN + off] = v;
+        } else {
+            A[(long long)i * g.sN + off] = v;
+            B[(long long)i * g.sN + off] = v;
+        }
     }
 }
 
-template <int Q, typename S>
-__global__ void k_get_pop(const S *__restrict__ A, Grid g, int i, double *__restrict__ f)
+template <int Q, typename S, int LAY = kLayAB>
+__global__ void k_get_pop(const S *__restrict__ A, const uint8_t *__restrict__ tags, Grid g, int i,
+                          double *__restrict__ f)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const int off = (z * g.ny + y) * g.px + x;
+    Nbr nb;
+    read_node<LAY>(nb, g, x, y, z);
     const long long n = x + (long long)g.nx * (y + (long long)g.ny * z);
     double w = 0.0;
 #pragma unroll
     for (int k = 0; k < Q; ++k)
         if (k == i) w = wgt<double>(Q, k);
-    f[n] = (double)Store<S>::ld(A + (long long)i * g.sN + off) + w;
+    // layout P: solid and wall nodes keep their (never updated) own slots
+    const bool nw = LAY == kLayP && (tags[nb.self] & kNearWall) != 0u;
+    const bool solid = LAY == kLayP && is_wall_tag(tags[nb.self] & kTagMask);
+    const long long o = solid ? (long long)opp(i) * g.sN + nb.self : fstar_off<LAY>(i, g, nb, nw, tags);
+    f[n] = (double)Store<S>::ld(A + o) + w;
 }
 
+// With aa, one array in layout S (slot opp(i) of the node); B is unused.
 template <int Q, typename S>
-__global__ void k_set_pop(S *__restrict__ A, S *__restrict__ B, Grid g, int i, const double *__restrict__ f)
+__global__ void k_set_pop(S *__restrict__ A, S *__restrict__ B, Grid g, int i, const double *__restrict__ f, bool aa)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -948,8 +1104,12 @@ __global__ void k_set_pop(S *__restrict__ A, S *__restrict__ B, Grid g, int i, c
     for (int k = 0; k < Q; ++k)
         if (k == i) w = wgt<double>(Q, k);
     const S v = Store<S>::from_f64(f[n] - w);
-    A[(long long)i * g.sN + off] = v;
-    B[(long long)i * g.sN + off] = v;
+    if (aa) {
+        A[(long long)opp(i) * g.sN + off] = v;
+    } else {
+        A[(long long)i * g.sN + off] = v;
+        B[(long long)i * g.sN + off] = v;
+    }
 }
 
 // Block shape shared by the node-per-thread kernels.
@@ -1004,8 +1164,10 @@ cudaError_t step_closure_x2(const Launch &L, const KParams<float> &kp, float *pa
     return cudaGetLastError();
 }
 
-// RED: fused step-and-reduce (FP32 compute; BGK, Smagorinsky and TRT).
-template <int Q, typename S, bool GEN, bool RED>
+// One dense step launch.  RED: fused step-and-reduce (FP32 compute; BGK,
+// Smagorinsky and TRT).  PAT: streaming pattern (the two-nodes-per-thread
+// 16-bit kernel is A/B only; AA steps take one node per thread).
+template <int Q, typename S, bool GEN, bool RED, int PAT>
 cudaError_t step_closure(const Launch &L, const KParams<typename Store<S>::T> &kp, dim3 grid, dim3 block,
                          float *partials)
 {
@@ -1017,29 +1179,29 @@ cudaError_t step_closure(const Launch &L, const KParams<typename Store<S>::T> &k
         if (L.closure == LBM_CLOSURE_MLP) {
             if (RED) return cudaErrorNotSupported;
             if (!L.mlp_image) return cudaErrorInvalidValue;
-            k_collide_stream_mlp<Q, S, GEN>
+            k_collide_stream_mlp<Q, S, GEN, PAT>
                 <<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, (const MlpSmem *)L.mlp_image);
             return cudaGetLastError();
         }
-        if constexpr (use_pairs<S>()) {
+        if constexpr (use_pairs<S>() && PAT == kPatAB) {
             if (L.g.px >= 64) return step_closure_x2<Q, S, GEN, RED>(L, kp, partials);
         }
         switch (L.closure) {
         case LBM_CLOSURE_BGK:
-            k_collide_stream<Q, S, GEN, LBM_CLOSURE_BGK, RED>
+            k_collide_stream<Q, S, GEN, LBM_CLOSURE_BGK, RED, PAT>
                 <<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, partials);
             break;
         case LBM_CLOSURE_SMAGORINSKY:
-            k_collide_stream<Q, S, GEN, LBM_CLOSURE_SMAGORINSKY, RED>
+            k_collide_stream<Q, S, GEN, LBM_CLOSURE_SMAGORINSKY, RED, PAT>
                 <<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, partials);
             break;
         case LBM_CLOSURE_TRT:
-            k_collide_stream<Q, S, GEN, LBM_CLOSURE_TRT, RED>
+            k_collide_stream<Q, S, GEN, LBM_CLOSURE_TRT, RED, PAT>
                 <<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, partials);
             break;
         case LBM_CLOSURE_STREAM_ONLY:
             if constexpr (RED) return cudaErrorNotSupported;
-            k_collide_stream<Q, S, GEN, LBM_CLOSURE_STREAM_ONLY, false>
+            k_collide_stream<Q, S, GEN, LBM_CLOSURE_STREAM_ONLY, false, PAT>
                 <<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, nullptr);
             break;
         default: return cudaErrorInvalidValue;
@@ -1052,29 +1214,60 @@ cudaError_t step_closure(const Launch &L, const KParams<typename Store<S>::T> &k
 inline long long fused_partials(const Launch &L, size_t elem)
 {
     dim3 grid, block;
-    if (elem == 2 && L.g.px >= 64)
+    if (elem == 2 && !L.aa && L.g.px >= 64)
         pair_launch_shape(L.g, grid, block);
     else
         node_launch_shape(L.g, grid, block);
     return (long long)grid.x * grid.y * grid.z;
 }
 
-template <int Q, typename S> cudaError_t step_q(const Launch &L, const lbm_params &p)
+template <int Q, typename S, int PAT> cudaError_t step_q(const Launch &L, const lbm_params &p)
 {
     dim3 grid, block;
     node_launch_shape(L.g, grid, block);
     const auto kp = make_kparams<typename Store<S>::T>(Q, p);
-    return L.general ? step_closure<Q, S, true, false>(L, kp, grid, block, nullptr)
-                     : step_closure<Q, S, false, false>(L, kp, grid, block, nullptr);
+    return L.general ? step_closure<Q, S, true, false, PAT>(L, kp, grid, block, nullptr)
+                     : step_closure<Q, S, false, false, PAT>(L, kp, grid, block, nullptr);
 }
 
-template <int Q, typename S> cudaError_t step_reduce_q(const Launch &L, const lbm_params &p, float *partials)
+template <int Q, typename S, int PAT> cudaError_t step_reduce_q(const Launch &L, const lbm_params &p, float *partials)
 {
     dim3 grid, block;
     node_launch_shape(L.g, grid, block);
     const auto kp = make_kparams<typename Store<S>::T>(Q, p);
-    return L.general ? step_closure<Q, S, true, true>(L, kp, grid, block, partials)
-                     : step_closure<Q, S, false, true>(L, kp, grid, block, partials);
+    return L.general ? step_closure<Q, S, true, true, PAT>(L, kp, grid, block, partials)
+                     : step_closure<Q, S, false, true, PAT>(L, kp, grid, block, partials);
+}
+
+template <int Q, typename S, int PAT>
+cudaError_t step_compact_q(const Launch &L, const lbm_params &p, const void *Ac, void *Bc, const int *nbr,
+                           long long nfp)
+{
+    const auto kp = make_kparams<typename Store<S>::T>(Q, p);
+    const unsigned blocks = (unsigned)((L.n_list + kStepThreads - 1) / kStepThreads);
+    if (blocks == 0) return cudaSuccess;
+    const S *A = (const S *)Ac;
+    S *B = (S *)Bc;
+    switch (L.closure) {
+    case LBM_CLOSURE_BGK:
+        k_collide_stream_compact<Q, S, LBM_CLOSURE_BGK, PAT>
+            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
+        break;
+    case LBM_CLOSURE_SMAGORINSKY:
+        k_collide_stream_compact<Q, S, LBM_CLOSURE_SMAGORINSKY, PAT>
+            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
+        break;
+    case LBM_CLOSURE_STREAM_ONLY:
+        k_collide_stream_compact<Q, S, LBM_CLOSURE_STREAM_ONLY, PAT>
+            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
+        break;
+    case LBM_CLOSURE_TRT:
+        k_collide_stream_compact<Q, S, LBM_CLOSURE_TRT, PAT>
+            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 // Blocks of `threads` threads of `kernel` that fit on the device at once.
@@ -1091,119 +1284,145 @@ template <typename K> int resident_blocks(K kernel, int threads)
 // nblocks (<= kRedBlocks) is cut to one resident wave: every block then
 // sweeps the same number of nodes at the same time, with no second, partly
 // filled wave.
-template <int Q, typename S>
+template <int Q, typename S, int LAY = kLayAB>
 cudaError_t reduce_q(const Launch &L, const lbm_params &p, double *partials, int nblocks, double *out)
 {
     const auto kp = make_kparams<typename Store<S>::T>(Q, p);
-    const int wave = L.general ? resident_blocks(k_reduce<Q, S, true>, kRedThreads)
-                               : resident_blocks(k_reduce<Q, S, false>, kRedThreads);
+    const int wave = L.general ? resident_blocks(k_reduce<Q, S, true, LAY>, kRedThreads)
+                               : resident_blocks(k_reduce<Q, S, false, LAY>, kRedThreads);
     if (wave > 0 && nblocks > wave) nblocks = wave;
     if (L.general)
-        k_reduce<Q, S, true><<<nblocks, kRedThreads, 0, L.stream>>>((const S *)L.A, L.tags, L.g, kp, partials);
+        k_reduce<Q, S, true, LAY><<<nblocks, kRedThreads, 0, L.stream>>>((const S *)L.A, L.tags, L.g, kp, partials);
     else
-        k_reduce<Q, S, false><<<nblocks, kRedThreads, 0, L.stream>>>((const S *)L.A, L.tags, L.g, kp, partials);
+        k_reduce<Q, S, false, LAY><<<nblocks, kRedThreads, 0, L.stream>>>((const S *)L.A, L.tags, L.g, kp, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce_final<<<1, kRedThreads, 0, L.stream>>>(partials, nblocks, out);
     return cudaGetLastError();
 }
 
-template <int Q, typename S> cudaError_t moments_q(const Launch &L, const lbm_params &p, double *rho, double *u)
+template <int Q, typename S, int LAY>
+cudaError_t moments_q(const Launch &L, const lbm_params &p, double *rho, double *u)
 {
     dim3 grid, block;
     node_launch_shape(L.g, grid, block);
     const auto kp = make_kparams<typename Store<S>::T>(Q, p);
     if (L.general)
-        k_moments<Q, S, true><<<grid, block, 0, L.stream>>>((const S *)L.A, L.tags, L.g, kp, rho, u);
+        k_moments<Q, S, true, LAY><<<grid, block, 0, L.stream>>>((const S *)L.A, L.tags, L.g, kp, rho, u);
     else
-        k_moments<Q, S, false><<<grid, block, 0, L.stream>>>((const S *)L.A, L.tags, L.g, kp, rho, u);
+        k_moments<Q, S, false, LAY><<<grid, block, 0, L.stream>>>((const S *)L.A, L.tags, L.g, kp, rho, u);
     return cudaGetLastError();
 }
 
-template <int Q, typename S>
-cudaError_t step_compact_q(const Launch &L, const lbm_params &p, const void *Ac, void *Bc, const int *nbr,
-                           long long nfp)
+template <int Q, typename S, int LAY> cudaError_t get_pop_q(const Launch &L, int i, double *f)
 {
-    const auto kp = make_kparams<typename Store<S>::T>(Q, p);
-    const unsigned blocks = (unsigned)((L.n_list + kStepThreads - 1) / kStepThreads);
-    if (blocks == 0) return cudaSuccess;
-    const S *A = (const S *)Ac;
-    S *B = (S *)Bc;
-    switch (L.closure) {
-    case LBM_CLOSURE_BGK:
-        k_collide_stream_compact<Q, S, LBM_CLOSURE_BGK>
-            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
-        break;
-    case LBM_CLOSURE_SMAGORINSKY:
-        k_collide_stream_compact<Q, S, LBM_CLOSURE_SMAGORINSKY>
-            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
-        break;
-    case LBM_CLOSURE_STREAM_ONLY:
-        k_collide_stream_compact<Q, S, LBM_CLOSURE_STREAM_ONLY>
-            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
-        break;
-    case LBM_CLOSURE_TRT:
-        k_collide_stream_compact<Q, S, LBM_CLOSURE_TRT>
-            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
-        break;
-    default: return cudaErrorInvalidValue;
-    }
+    dim3 grid, block;
+    node_launch_shape(L.g, grid, block);
+    k_get_pop<Q, S, LAY><<<grid, block, 0, L.stream>>>((const S *)L.A, L.tags, L.g, i, f);
     return cudaGetLastError();
 }
 
+// The AA instantiations (one array, steps alternating odd / even; reads in
+// layout S or P), kept in translation units of their own.
+#define LBM_DEFINE_AA_LAUNCHERS(S)                                                                           \
+    template <> cudaError_t launch_step_aa<S>(const Launch &L, const lbm_params &p)                          \
+    {                                                                                                        \
+        if (L.aa_p) return L.Q == 19 ? step_q<19, S, kPatAAEven>(L, p) : step_q<27, S, kPatAAEven>(L, p);    \
+        return L.Q == 19 ? step_q<19, S, kPatAAOdd>(L, p) : step_q<27, S, kPatAAOdd>(L, p);                  \
+    }                                                                                                        \
+    template <> cudaError_t launch_step_reduce_aa<S>(const Launch &L, const lbm_params &p, float *partials)  \
+    {                                                                                                        \
+        if (L.aa_p)                                                                                          \
+            return L.Q == 19 ? step_reduce_q<19, S, kPatAAEven>(L, p, partials)                              \
+                             : step_reduce_q<27, S, kPatAAEven>(L, p, partials);                             \
+        return L.Q == 19 ? step_reduce_q<19, S, kPatAAOdd>(L, p, partials)                                   \
+                         : step_reduce_q<27, S, kPatAAOdd>(L, p, partials);                                  \
+    }                                                                                                        \
+    template <>                                                                                              \
+    cudaError_t launch_step_compact_aa<S>(const Launch &L, const lbm_params &p, const void *Ac, void *Bc,    \
+                                          const int *nbr, long long nfp)                                     \
+    {                                                                                                        \
+        if (L.aa_p)                                                                                          \
+            return L.Q == 19 ? step_compact_q<19, S, kPatAAEven>(L, p, Ac, Bc, nbr, nfp)                     \
+                             : step_compact_q<27, S, kPatAAEven>(L, p, Ac, Bc, nbr, nfp);                    \
+        return L.Q == 19 ? step_compact_q<19, S, kPatAAOdd>(L, p, Ac, Bc, nbr, nfp)                          \
+                         : step_compact_q<27, S, kPatAAOdd>(L, p, Ac, Bc, nbr, nfp);                         \
+    }                                                                                                        \
+    template <>                                                                                              \
+    cudaError_t launch_reduce_aa<S>(const Launch &L, const lbm_params &p, double *partials, int nb, double *out) \
+    {                                                                                                        \
+        if (L.aa_p)                                                                                          \
+            return L.Q == 19 ? reduce_q<19, S, kLayP>(L, p, partials, nb, out)                               \
+                             : reduce_q<27, S, kLayP>(L, p, partials, nb, out);                              \
+        return L.Q == 19 ? reduce_q<19, S, kLayS>(L, p, partials, nb, out)                                   \
+                         : reduce_q<27, S, kLayS>(L, p, partials, nb, out);                                  \
+    }                                                                                                        \
+    template <> cudaError_t launch_moments_aa<S>(const Launch &L, const lbm_params &p, double *rho, double *u) \
+    {                                                                                                        \
+        if (L.aa_p) return L.Q == 19 ? moments_q<19, S, kLayP>(L, p, rho, u) : moments_q<27, S, kLayP>(L, p, rho, u); \
+        return L.Q == 19 ? moments_q<19, S, kLayS>(L, p, rho, u) : moments_q<27, S, kLayS>(L, p, rho, u);    \
+    }                                                                                                        \
+    template <> cudaError_t launch_get_pop_aa<S>(const Launch &L, int i, double *f)                          \
+    {                                                                                                        \
+        if (L.aa_p) return L.Q == 19 ? get_pop_q<19, S, kLayP>(L, i, f) : get_pop_q<27, S, kLayP>(L, i, f);  \
+        return L.Q == 19 ? get_pop_q<19, S, kLayS>(L, i, f) : get_pop_q<27, S, kLayS>(L, i, f);              \
+    }
+
+// The A/B instantiations, and the entry points that dispatch AA launches to
+// the functions above.
 #define LBM_DEFINE_LAUNCHERS(S)                                                                              \
     template <> cudaError_t launch_step_reduce<S>(const Launch &L, const lbm_params &p, float *partials)     \
     {                                                                                                        \
-        return L.Q == 19 ? step_reduce_q<19, S>(L, p, partials) : step_reduce_q<27, S>(L, p, partials);     \
+        if (L.aa) return launch_step_reduce_aa<S>(L, p, partials);                                           \
+        return L.Q == 19 ? step_reduce_q<19, S, kPatAB>(L, p, partials) : step_reduce_q<27, S, kPatAB>(L, p, partials); \
     }                                                                                                        \
     template <>                                                                                              \
     cudaError_t launch_step_compact<S>(const Launch &L, const lbm_params &p, const void *Ac, void *Bc,       \
                                        const int *nbr, long long nfp)                                        \
     {                                                                                                        \
-        return L.Q == 19 ? step_compact_q<19, S>(L, p, Ac, Bc, nbr, nfp)                                    \
-                         : step_compact_q<27, S>(L, p, Ac, Bc, nbr, nfp);                                   \
+        if (L.aa) return launch_step_compact_aa<S>(L, p, Ac, Bc, nbr, nfp);                                  \
+        return L.Q == 19 ? step_compact_q<19, S, kPatAB>(L, p, Ac, Bc, nbr, nfp)                             \
+                         : step_compact_q<27, S, kPatAB>(L, p, Ac, Bc, nbr, nfp);                            \
     }                                                                                                        \
     template <> cudaError_t launch_step<S>(const Launch &L, const lbm_params &p)                             \
     {                                                                                                        \
-        return L.Q == 19 ? step_q<19, S>(L, p) : step_q<27, S>(L, p);                                       \
+        if (L.aa) return launch_step_aa<S>(L, p);                                                            \
+        return L.Q == 19 ? step_q<19, S, kPatAB>(L, p) : step_q<27, S, kPatAB>(L, p);                        \
     }                                                                                                        \
     template <>                                                                                              \
     cudaError_t launch_reduce<S>(const Launch &L, const lbm_params &p, double *partials, int nb, double *out) \
     {                                                                                                        \
+        if (L.aa) return launch_reduce_aa<S>(L, p, partials, nb, out);                                       \
         return L.Q == 19 ? reduce_q<19, S>(L, p, partials, nb, out) : reduce_q<27, S>(L, p, partials, nb, out); \
     }                                                                                                        \
     template <> cudaError_t launch_moments<S>(const Launch &L, const lbm_params &p, double *rho, double *u)  \
     {                                                                                                        \
-        return L.Q == 19 ? moments_q<19, S>(L, p, rho, u) : moments_q<27, S>(L, p, rho, u);                 \
+        if (L.aa) return launch_moments_aa<S>(L, p, rho, u);                                                 \
+        return L.Q == 19 ? moments_q<19, S, kLayAB>(L, p, rho, u) : moments_q<27, S, kLayAB>(L, p, rho, u);  \
     }                                                                                                        \
     template <> cudaError_t launch_init<S>(const Launch &L, const double *rho, const double *u)              \
     {                                                                                                        \
         dim3 grid, block;                                                                                    \
         node_launch_shape(L.g, grid, block);                                                                 \
         if (L.Q == 19)                                                                                       \
-            k_init<19, S><<<grid, block, 0, L.stream>>>((S *)L.A, (S *)L.B, L.g, rho, u);                    \
+            k_init<19, S><<<grid, block, 0, L.stream>>>((S *)L.A, (S *)L.B, L.g, rho, u, L.aa);              \
         else                                                                                                 \
-            k_init<27, S><<<grid, block, 0, L.stream>>>((S *)L.A, (S *)L.B, L.g, rho, u);                    \
+            k_init<27, S><<<grid, block, 0, L.stream>>>((S *)L.A, (S *)L.B, L.g, rho, u, L.aa);              \
         return cudaGetLastError();                                                                           \
     }                                                                                                        \
     template <> cudaError_t launch_get_pop<S>(const Launch &L, int i, double *f)                             \
     {                                                                                                        \
-        dim3 grid, block;                                                                                    \
-        node_launch_shape(L.g, grid, block);                                                                 \
-        if (L.Q == 19)                                                                                       \
-            k_get_pop<19, S><<<grid, block, 0, L.stream>>>((const S *)L.A, L.g, i, f);                       \
-        else                                                                                                 \
-            k_get_pop<27, S><<<grid, block, 0, L.stream>>>((const S *)L.A, L.g, i, f);                       \
-        return cudaGetLastError();                                                                           \
+        if (L.aa) return launch_get_pop_aa<S>(L, i, f);                                                      \
+        return L.Q == 19 ? get_pop_q<19, S, kLayAB>(L, i, f) : get_pop_q<27, S, kLayAB>(L, i, f);            \
     }                                                                                                        \
     template <> cudaError_t launch_set_pop<S>(const Launch &L, int i, const double *f)                       \
     {                                                                                                        \
         dim3 grid, block;                                                                                    \
         node_launch_shape(L.g, grid, block);                                                                 \
         if (L.Q == 19)                                                                                       \
-            k_set_pop<19, S><<<grid, block, 0, L.stream>>>((S *)L.A, (S *)L.B, L.g, i, f);                   \
+            k_set_pop<19, S><<<grid, block, 0, L.stream>>>((S *)L.A, (S *)L.B, L.g, i, f, L.aa);            \
         else                                                                                                 \
-            k_set_pop<27, S><<<grid, block, 0, L.stream>>>((S *)L.A, (S *)L.B, L.g, i, f);                   \
+            k_set_pop<27, S><<<grid, block, 0, L.stream>>>((S *)L.A, (S *)L.B, L.g, i, f, L.aa);            \
         return cudaGetLastError();                                                                           \
     }
 

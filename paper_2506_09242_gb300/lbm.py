@@ -20,6 +20,8 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_UNSTABLE, ERR_TIMEOUT = range(7)
 D3Q19, D3Q27 = 19, 27
 F64, F32, F16_SHIFTED, BF16_SHIFTED = 0, 1, 2, 3
 DTYPES = {"f64": F64, "f32": F32, "f16": F16_SHIFTED, "bf16": BF16_SHIFTED}
+PATTERN_AB, PATTERN_AA = 0, 1
+PATTERNS = {"ab": PATTERN_AB, "aa": PATTERN_AA}
 TAG_FLUID, TAG_FORCED, TAG_SOLID, TAG_WALL0, NWALLS = 0, 1, 2, 3, 8
 NTAGS = TAG_WALL0 + NWALLS
 CLOSURE_BGK, CLOSURE_SMAGORINSKY, CLOSURE_MLP, CLOSURE_STREAM_ONLY, CLOSURE_TRT = 0, 1, 2, 3, 4
@@ -82,6 +84,7 @@ class Allocator(ctypes.Structure):
 _P, _I, _D, _LL, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_size_t
 SIGNATURES = {
     "lbm_create": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(Allocator), _P, ctypes.POINTER(_P)]),
+    "lbm_create_ex": (_I, [_I, _I, _I, _I, _I, _I, ctypes.POINTER(Allocator), _P, ctypes.POINTER(_P)]),
     "lbm_destroy": (_I, [_P]),
     "lbm_set_params": (_I, [_P, ctypes.POINTER(Params)]),
     "lbm_set_tags": (_I, [_P, _P, _I]),
@@ -194,8 +197,9 @@ class Lattice:
     """
 
     def __init__(self, nx: int, ny: int, nz: int, lattice: int = D3Q19, dtype="f32", *, device: int = 0,
-                 stream=None, torch_allocator: bool = True):
+                 stream=None, torch_allocator: bool = True, pattern: str = "ab"):
         lib = load()
+        self.pattern = PATTERNS[pattern] if isinstance(pattern, str) else int(pattern)
         self.nx, self.ny, self.nz = nx, ny, nz
         self.Q = int(lattice)
         self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
@@ -216,7 +220,8 @@ class Lattice:
         self._stream = stream
         ctx = ctypes.c_void_p()
         alloc_ptr = ctypes.byref(self._alloc.struct) if self._alloc else None
-        _check(lib.lbm_create(nx, ny, nz, self.Q, self.dtype, alloc_ptr, stream_handle, ctypes.byref(ctx)))
+        _check(lib.lbm_create_ex(nx, ny, nz, self.Q, self.dtype, self.pattern, alloc_ptr, stream_handle,
+                                 ctypes.byref(ctx)))
         self._ctx = ctx
         self.params = Params()
         self.params.tau = 1.0

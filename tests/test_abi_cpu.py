@@ -51,6 +51,10 @@ def test_create_rejects_bad_arguments(lib):
         assert not out.value
         assert lib.lbm_last_error(None)
     assert lib.lbm_create(4, 4, 4, 19, 1, None, None, None) == lbm.ERR_ARG
+    for pattern in (-1, 2, 7):  # streaming pattern: AB (0) or AA (1) only
+        assert lib.lbm_create_ex(4, 4, 4, 19, 1, pattern, None, None, ctypes.byref(out)) == lbm.ERR_ARG
+        assert not out.value
+        assert b"pattern" in lib.lbm_last_error(None)
 
 
 def test_allocator_failure_is_reported_as_oom(lib):
