@@ -28,7 +28,7 @@ _LIB = _HERE / "_build" / "liblbm_oracle.so"
 FLUID, FORCED, SOLID, WALL0 = 0, 1, 2, 3
 NWALLS = 8
 BGK, SMAGORINSKY, MLP, STREAM_ONLY, TRT = 0, 1, 2, 3, 4
-F64, F32, F16, BF16 = 0, 1, 2, 3
+F64, F32, F16, BF16, F16_SCALED = 0, 1, 2, 3, 4
 MLP_NPARAM = 32 * 7 + 32 + 32 * 32 + 32 + 32 + 1
 
 

@@ -70,7 +70,7 @@ static int is_wall_or_solid(unsigned char t) { return t >= ORC_SOLID && t < ORC_
 enum { ORC_BGK = 0, ORC_SMAGORINSKY = 1, ORC_MLP = 2, ORC_STREAM_ONLY = 3, ORC_TRT = 4 };
 
 /* Storage emulation. */
-enum { ORC_F64 = 0, ORC_F32 = 1, ORC_F16 = 2, ORC_BF16 = 3 };
+enum { ORC_F64 = 0, ORC_F32 = 1, ORC_F16 = 2, ORC_BF16 = 3, ORC_F16_SCALED = 4 };
 
 /* Number of MLP parameters: W1[32][7] b1[32] W2[32][32] b2[32] w3[32] b3. */
 #define ORC_MLP_IN 7
@@ -207,6 +207,9 @@ static double round_to(double h, int dtype)
     case ORC_F32: return (double)(float)h;
     case ORC_F16: return (double)(_Float16)(float)h;
     case ORC_BF16: return (double)to_bf16_float((float)h);
+    /* FP16 of h times 2^12: a power-of-two scale is exact in binary floating
+     * point, so only the half-precision rounding of the scaled value acts. */
+    case ORC_F16_SCALED: return ldexp((double)(_Float16)(float)ldexp(h, 12), -12);
     default: return h;
     }
 }

@@ -95,6 +95,29 @@ def test_storage_rounding_matches_library_routines():
         assert oracle.round_scalar(h[k], oracle.F64) == h[k]
 
 
+def test_scaled_fp16_rounding():
+    """FP16 of h * 2^12: the library conversion of the scaled value, a
+    relative error within half an FP16 ulp (2^-11) for every |h| from 2^-26
+    (the scaled normal threshold) up to 16, where plain FP16 goes subnormal
+    below 6.1e-5 and loses that bound, and overflow to infinity from 16 on."""
+    rng = np.random.default_rng(12)
+    h = np.concatenate([rng.normal(scale=s, size=2000) for s in (1e-1, 1e-3, 1e-5, 1e-7)])
+    lib16 = np.float16(np.float32(h) * np.float32(4096.0)).astype(np.float64) / 4096.0
+    mag = np.abs(h)
+    for k in range(len(h)):
+        r = oracle.round_scalar(h[k], oracle.F16_SCALED)
+        assert r == lib16[k]
+        if 2.0 ** -26 <= mag[k] < 16.0:
+            assert abs(r - h[k]) <= 2.0 ** -11 * mag[k]
+    tiny = h[(mag > 1e-7) & (mag < 2e-6)]
+    plain = np.array([oracle.round_scalar(v, oracle.F16) for v in tiny])
+    assert np.max(np.abs(plain - tiny) / np.abs(tiny)) > 1e-2  # subnormal FP16
+    assert oracle.round_scalar(16.0, oracle.F16_SCALED) == np.inf
+    assert oracle.round_scalar(-16.5, oracle.F16_SCALED) == -np.inf
+    assert oracle.round_scalar(15.99, oracle.F16_SCALED) == pytest.approx(15.99, rel=2.0 ** -11)
+    assert oracle.round_scalar(2.0 ** -30, oracle.F16_SCALED) == 2.0 ** -30  # scaled 2^-18: exact subnormal
+
+
 def test_round_storage_keeps_offset():
     c, w, _ = oracle.lattice(19)
     f = w[:, None] * (1.0 + np.linspace(-0.1, 0.1, 7)[None, :])
