@@ -44,7 +44,7 @@ if str(ROOT) not in sys.path:
 
 METRIC = "GLUPS per GB300 vs HBM roofline; FP32 vs FP16-shifted storage at stated error"
 UNIT = "GLUPS"
-SIZE = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+SIZE = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "f16s": 2}
 
 
 # ---------------------------------------------------------------------------
@@ -330,7 +330,7 @@ def run_reference(args):
     return 0
 
 
-def error_vs_f64(dtypes=("f32", "f16", "bf16"), n=64, steps=400):
+def error_vs_f64(dtypes=("f32", "f16", "bf16", "f16s"), n=64, steps=400):
     """Velocity relative L2 error of each storage type against the FP64 run of
     the same lattice (periodic 3D TGV n^3, D3Q19, u0 = 0.04, Re = 1600 at n)."""
     import numpy as np
@@ -406,7 +406,8 @@ def run_ours(args):
                                 ("tgv128_d3q19", "f32", "mlp", "ab"), ("porous400_d3q19", "f32", "bgk", "ab"),
                                 ("porous400_d3q19", "f16", "bgk", "ab"), ("tgv512_d3q19", "f32", "bgk", "aa"),
                                 ("tgv512_d3q19", "f16", "bgk", "aa"), ("cavity256_d3q19", "f32", "bgk", "aa"),
-                                ("porous400_d3q19", "f32", "bgk", "aa")):
+                                ("porous400_d3q19", "f32", "bgk", "aa"), ("tgv512_d3q19", "f16s", "bgk", "ab"),
+                                ("tgv512_d3q27", "f16s", "bgk", "ab")):
             if (wl, dt, cl, pat) == (args.workload, args.dtype, args.closure, args.pattern):
                 continue
             v, _, d = make_workload(wl, dt, cl, pat)

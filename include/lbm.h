@@ -55,8 +55,13 @@ typedef enum { LBM_D3Q19 = 19, LBM_D3Q27 = 27 } lbm_lattice;
 /* Storage type of the populations.  Every type stores the offset-stripped
  * deviation h_i = f_i - w_i (Skordos' shift, Sec. 3); arithmetic runs in FP64
  * for LBM_F64 and in FP32 for the others; reductions accumulate in FP64.
- * The 16-bit types round to nearest-even on store. */
-typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16_SHIFTED = 2, LBM_BF16_SHIFTED = 3 } lbm_dtype;
+ * The 16-bit types round to nearest-even on store.  LBM_F16_SCALED stores
+ * FP16 of h * 2^12: the same 11 significant bits as LBM_F16_SHIFTED, with
+ * the subnormal range moved from |h| < 6.1e-5 down to |h| < 1.5e-8 (where
+ * a decaying flow's density and velocity deviations end up) and the largest
+ * storable |h| at 16 (f lies in [0, rho], so only an unstable state gets
+ * there: it becomes infinite and lbm_reduce reports it). */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16_SHIFTED = 2, LBM_BF16_SHIFTED = 3, LBM_F16_SCALED = 4 } lbm_dtype;
 
 /* Streaming pattern (Sec. 2.3.1 names both; the paper's port uses the
  * two-population scheme and leaves the AA pattern to future work).

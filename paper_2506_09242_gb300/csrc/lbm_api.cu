@@ -154,6 +154,7 @@ template <typename F> cudaError_t by_dtype(lbm_dtype d, F &&f)
     case LBM_F32: return f((float *)nullptr);
     case LBM_F16_SHIFTED: return f((__half *)nullptr);
     case LBM_BF16_SHIFTED: return f((__nv_bfloat16 *)nullptr);
+    case LBM_F16_SCALED: return f((h16s *)nullptr);
     }
     return cudaErrorInvalidValue;
 }
@@ -475,7 +476,7 @@ lbm_status lbm_create_ex(int nx, int ny, int nz, lbm_lattice lattice, lbm_dtype 
         return fail(nullptr, LBM_ERR_ARG, "unknown streaming pattern %d", (int)pattern);
     if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_ERR_ARG, "lattice sizes must be >= 1");
     if (lattice != LBM_D3Q19 && lattice != LBM_D3Q27) return fail(nullptr, LBM_ERR_ARG, "unknown lattice %d", (int)lattice);
-    if (dtype < LBM_F64 || dtype > LBM_BF16_SHIFTED) return fail(nullptr, LBM_ERR_ARG, "unknown dtype %d", (int)dtype);
+    if (dtype < LBM_F64 || dtype > LBM_F16_SCALED) return fail(nullptr, LBM_ERR_ARG, "unknown dtype %d", (int)dtype);
     if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, LBM_ERR_ARG, "allocator needs alloc and free");
     if (nz > 65535) return fail(nullptr, LBM_ERR_ARG, "nz must be <= 65535");
     const long long px = ((long long)nx + 31) / 32 * 32;

@@ -86,6 +86,21 @@ template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ T rt(T v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 };
 
+// FP16 of h * 2^12 (LBM_F16_SCALED).  Power-of-two scaling is exact in FP32,
+// so the stored value is the FP16 rounding of the scaled deviation.
+struct h16s {
+    __half v;
+};
+constexpr float kF16sUp = 4096.0f, kF16sDown = 1.0f / 4096.0f;
+template <> struct Store<h16s> {
+    using T = float;
+    static __device__ __forceinline__ T ld(const h16s *p) { return __half2float(__ldg(&p->v)) * kF16sDown; }
+    static __device__ __forceinline__ T ldc(const h16s *p) { return __half2float(p->v) * kF16sDown; }
+    static __device__ __forceinline__ void st(h16s *p, T v) { p->v = __float2half_rn(v * kF16sUp); }
+    static __device__ __forceinline__ h16s from_f64(double v) { return h16s{__float2half_rn((float)v * kF16sUp)}; }
+    static __device__ __forceinline__ T rt(T v) { return __half2float(__float2half_rn(v * kF16sUp)) * kF16sDown; }
+};
+
 // Fluid-node list (lattices that are mostly wall): link mask of each listed
 // node, bit i set when the pull source of direction i is SOLID or WALL.
 constexpr uint32_t kListForced = 1u << 30;   // the node carries the body force

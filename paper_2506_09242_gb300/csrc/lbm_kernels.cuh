@@ -752,6 +752,18 @@ template <> struct Pair<__nv_bfloat16> {
         *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
     }
 };
+template <> struct Pair<h16s> {
+    static __device__ __forceinline__ float2 ld(const h16s *p)
+    {
+        const unsigned v = __ldg(reinterpret_cast<const unsigned *>(p));
+        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&v));
+        return make_float2(f.x * kF16sDown, f.y * kF16sDown);
+    }
+    static __device__ __forceinline__ void st(h16s *p, float a, float b)
+    {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a * kF16sUp, b * kF16sUp);
+    }
+};
 template <> struct Pair<float> {
     static __device__ __forceinline__ float2 ld(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
     static __device__ __forceinline__ void st(float *p, float a, float b)

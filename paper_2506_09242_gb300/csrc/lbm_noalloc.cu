@@ -81,7 +81,7 @@ extern "C" lbm_status lbm_reduce_noalloc(const void *h, lbm_lattice lattice, lbm
 {
     if (!h || !out) return fail(LBM_ERR_ARG, "lbm_reduce_noalloc: NULL populations or output");
     if (lattice != LBM_D3Q19 && lattice != LBM_D3Q27) return fail(LBM_ERR_ARG, "lbm_reduce_noalloc: unknown lattice");
-    if (dtype < LBM_F64 || dtype > LBM_BF16_SHIFTED) return fail(LBM_ERR_ARG, "lbm_reduce_noalloc: unknown dtype");
+    if (dtype < LBM_F64 || dtype > LBM_F16_SCALED) return fail(LBM_ERR_ARG, "lbm_reduce_noalloc: unknown dtype");
     if (nx < 1 || ny < 1 || nz < 1) return fail(LBM_ERR_ARG, "lbm_reduce_noalloc: lattice sizes must be >= 1");
     const long long N = (long long)nx * ny * nz;
     if (N > (long long)LBM_NOALLOC_MAX_NODES)
@@ -116,6 +116,9 @@ extern "C" lbm_status lbm_reduce_noalloc(const void *h, lbm_lattice lattice, lbm
     case LBM_F32: e = L.Q == 19 ? reduce_q<19, float>(L, p, partials, (int)nb, sums) : reduce_q<27, float>(L, p, partials, (int)nb, sums); break;
     case LBM_F16_SHIFTED:
         e = L.Q == 19 ? reduce_q<19, __half>(L, p, partials, (int)nb, sums) : reduce_q<27, __half>(L, p, partials, (int)nb, sums);
+        break;
+    case LBM_F16_SCALED:
+        e = L.Q == 19 ? reduce_q<19, h16s>(L, p, partials, (int)nb, sums) : reduce_q<27, h16s>(L, p, partials, (int)nb, sums);
         break;
     default:
         e = L.Q == 19 ? reduce_q<19, __nv_bfloat16>(L, p, partials, (int)nb, sums)

@@ -18,8 +18,8 @@ _LIB_PATH = Path(__file__).resolve().parent / "_lib" / "liblbm.so"
 # Values of include/lbm.h.
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_UNSTABLE, ERR_TIMEOUT = range(7)
 D3Q19, D3Q27 = 19, 27
-F64, F32, F16_SHIFTED, BF16_SHIFTED = 0, 1, 2, 3
-DTYPES = {"f64": F64, "f32": F32, "f16": F16_SHIFTED, "bf16": BF16_SHIFTED}
+F64, F32, F16_SHIFTED, BF16_SHIFTED, F16_SCALED = 0, 1, 2, 3, 4
+DTYPES = {"f64": F64, "f32": F32, "f16": F16_SHIFTED, "bf16": BF16_SHIFTED, "f16s": F16_SCALED}
 PATTERN_AB, PATTERN_AA = 0, 1
 PATTERNS = {"ab": PATTERN_AB, "aa": PATTERN_AA}
 TAG_FLUID, TAG_FORCED, TAG_SOLID, TAG_WALL0, NWALLS = 0, 1, 2, 3, 8

@@ -115,7 +115,7 @@ def cavity(n: int = 256, *, re: float = 1000.0, u_lid: float = 0.1, steps: int =
             "ux_centreline_z": u[0, :, mid, mid][:: max(1, n // 16)].tolist()}
 
 
-def tgv_precision(n: int = 512, Q: int = 27, *, dtypes=("f64", "f32", "f16", "bf16"), u0: float = 0.04,
+def tgv_precision(n: int = 512, Q: int = 27, *, dtypes=("f64", "f32", "f16", "bf16", "f16s"), u0: float = 0.04,
                   re: float = 1600.0, t_end: float = 10.0, every: float = 0.5, error_at=(1.0, 5.0, 10.0)) -> dict:
     """Runs the TGV once per storage type (FP64 first) and compares each
     velocity field with the FP64 one at the times in error_at."""

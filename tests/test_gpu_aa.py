@@ -105,7 +105,7 @@ def test_aa_d3q27_and_degenerate_rows(Q):
             assert_same(a, b)
 
 
-@pytest.mark.parametrize("kind", ["f16", "bf16"])
+@pytest.mark.parametrize("kind", ["f16", "bf16", "f16s"])
 @pytest.mark.parametrize("nx", [32, 96])
 def test_aa_half_storage(kind, nx):
     """Rows padded to 32 nodes: both patterns take the one-node kernel
@@ -121,8 +121,9 @@ def test_aa_half_storage(kind, nx):
             assert_same(a, b)
         else:
             fa, fb = a[0], b[0]
-            ulp = 2.0 ** (-10 if kind == "f16" else -7)
-            assert np.all(np.abs(fa - fb) <= ulp * np.maximum(np.abs(fa), 6.1e-5) + 1e-12)
+            ulp = 2.0 ** (-7 if kind == "bf16" else -10)
+            tiny = {"f16": 6.1e-5, "bf16": 1e-30, "f16s": 1.5e-8}[kind]
+            assert np.all(np.abs(fa - fb) <= ulp * np.maximum(np.abs(fa), tiny) + 1e-12)
             assert np.mean(fa == fb) >= 0.99
 
 

@@ -24,7 +24,7 @@ from paper_2506_09242_gb300 import lbm
 
 pytestmark = pytest.mark.gpu
 
-DT = {"f64": oracle.F64, "f32": oracle.F32, "f16": oracle.F16, "bf16": oracle.BF16}
+DT = {"f64": oracle.F64, "f32": oracle.F32, "f16": oracle.F16, "bf16": oracle.BF16, "f16s": oracle.F16_SCALED}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -397,10 +397,14 @@ def test_f32_smagorinsky_velocity_l2(Q):
 # FP16 / BF16 shifted storage
 # ---------------------------------------------------------------------------
 def ulp(h, kind):
-    mant = 10 if kind == "f16" else 7
+    """Spacing of the stored values of h: FP16 below 2^-14 and scaled FP16
+    (h * 2^12) below 2^-26 have the fixed spacing of their subnormals."""
+    mant = 7 if kind == "bf16" else 10
     e = np.floor(np.log2(np.maximum(np.abs(h), 1e-300)))
     if kind == "f16":
         e = np.maximum(e, -14)
+    if kind == "f16s":
+        e = np.maximum(e, -26)
     return np.exp2(e - mant)
 
 
@@ -411,7 +415,7 @@ HALF_SHAPES = [(10, 12, 50), (5, 7, 45), (4, 6, 150), (3, 5, 64), (6, 5, 31)]
 
 
 @pytest.mark.parametrize("shape", HALF_SHAPES)
-@pytest.mark.parametrize("kind", ["f16", "bf16"])
+@pytest.mark.parametrize("kind", ["f16", "bf16", "f16s"])
 @pytest.mark.parametrize("Q", [19, 27])
 @pytest.mark.parametrize("mix", ["dense", "list"])
 def test_half_storage_one_step(kind, Q, shape, mix):
@@ -438,7 +442,7 @@ def test_half_storage_one_step(kind, Q, shape, mix):
 
 
 @pytest.mark.parametrize("shape", HALF_SHAPES)
-@pytest.mark.parametrize("kind", ["f16", "bf16"])
+@pytest.mark.parametrize("kind", ["f16", "bf16", "f16s"])
 @pytest.mark.parametrize("Q,closure", [(19, lbm.CLOSURE_BGK), (27, lbm.CLOSURE_BGK), (19, lbm.CLOSURE_SMAGORINSKY),
                                        (27, lbm.CLOSURE_TRT)])
 def test_half_storage_one_step_periodic(kind, Q, closure, shape):
@@ -462,7 +466,7 @@ def test_half_storage_one_step_periodic(kind, Q, closure, shape):
     lat.close()
 
 
-@pytest.mark.parametrize("kind", ["f16", "bf16"])
+@pytest.mark.parametrize("kind", ["f16", "bf16", "f16s"])
 def test_half_storage_error_after_200_steps_is_bounded(kind):
     """Error statement (not bit parity): 2D TGV config at 32^3 after 200 steps,
     velocity relative L2 against the FP64 oracle; the bound is a sanity limit."""
@@ -478,6 +482,27 @@ def test_half_storage_error_after_200_steps_is_bounded(kind):
     print(f"{kind}: velocity rel L2 after 200 steps = {err:.3e}")
     assert err <= (0.5 if kind == "bf16" else 5e-2)
     lat.close()
+
+
+def test_scaled_fp16_keeps_small_deviations():
+    """A 2D TGV of amplitude 2e-4 (|h| ~ 2e-5, inside plain FP16's subnormal
+    range): scaled FP16 keeps 11 significant bits there and must cut the
+    velocity error against the FP64 oracle well below plain FP16's."""
+    n = 32
+    rho, u = inp.tgv2d(n, n, n, 2e-4)
+    prob = oracle_problem((n, n, n), tau=0.8)
+    _, ur = prob.moments(prob.step(prob.init_equilibrium(rho, u), 100))
+    err = {}
+    for kind in ("f16", "f16s"):
+        lat = make((n, n, n), 19, kind, tau=0.8)
+        lat.init_equilibrium(rho, u)
+        lat.step(100)
+        _, ug = lat.moments()
+        err[kind] = rel_l2(ug, ur)
+        lat.close()
+    print(f"velocity rel L2 after 100 steps at u0 = 2e-4: {err}")
+    assert err["f16s"] < 0.25 * err["f16"]
+    assert err["f16s"] < 2e-2
 
 
 # ---------------------------------------------------------------------------
