@@ -56,6 +56,7 @@ class Params(ctypes.Structure):
         ("mlp_norm", ctypes.POINTER(ctypes.c_double)),
         ("mlp_bf16", ctypes.c_int),
         ("trt_magic", ctypes.c_double),
+        ("wall_rho_local", ctypes.c_int),
     ]
 
 
@@ -158,7 +159,7 @@ class Problem:
     def __init__(self, Q: int, nx: int, ny: int, nz: int, tags=None, *, tau: float,
                  force=(0.0, 0.0, 0.0), closure: int = BGK, cs_smag: float = 0.0,
                  wall_u=None, rho_wall: float = 1.0, mlp_params=None, mlp_norm=None,
-                 mlp_bf16: bool = False, trt_magic: float = 3.0 / 16.0):
+                 mlp_bf16: bool = False, trt_magic: float = 3.0 / 16.0, wall_rho_local: bool = False):
         self.Q, self.nx, self.ny, self.nz = Q, nx, ny, nz
         self.tags = None if tags is None else np.ascontiguousarray(tags, dtype=np.uint8).reshape(nz, ny, nx)
         self.p = Params()
@@ -172,6 +173,7 @@ class Problem:
                 for a in range(3):
                     self.p.wall_u[k][a] = v[a]
         self.p.rho_wall = rho_wall
+        self.p.wall_rho_local = 1 if wall_rho_local else 0
         self._mlp = None if mlp_params is None else _f64(mlp_params)
         self._norm = None if mlp_norm is None else _f64(mlp_norm)
         if self._mlp is not None:

@@ -88,6 +88,7 @@ typedef struct {
     const double *mlp_norm;          /* mean[7], std[7], out_scale, unused  */
     int mlp_bf16;                    /* 1: round MLP operands to bf16       */
     double trt_magic;                /* TRT: Lambda = (tau+ - 1/2)(tau- - 1/2) */
+    int wall_rho_local;              /* 1: rho_wall = the node's own density  */
 } orc_params;
 
 typedef struct {
@@ -335,7 +336,12 @@ static long long wrap(long long a, long long n) { return ((a % n) + n) % n; }
  *          = f*_{opp i}(x)                                    if it is SOLID,
  *          = f*_{opp i}(x) + 6 w_i rho_wall (c_i . u_wall_k)   if it is WALL_k,
  *   after which the node collides and its post-collision set is written to
- *   fout.  Solid and wall nodes are not updated (fout = fin there). */
+ *   fout.  Solid and wall nodes are not updated (fout = fin there).
+ *   With wall_rho_local, rho_wall is the node's own density after this
+ *   streaming, rho = sum_i f_i(x).  The wall terms are linear in it:
+ *   rho = rho0 + rho s, with rho0 the sum without them and s the sum of
+ *   6 w_i (c_i . u_wall_k) over the node's wall links, so
+ *   rho = rho0 / (1 - s). */
 int orc_step(int Q, int nx, int ny, int nz, const unsigned char *tags, const orc_params *p, const double *fin,
              double *fout)
 {
@@ -352,8 +358,10 @@ int orc_step(int Q, int nx, int ny, int nz, const unsigned char *tags, const orc
                     for (int i = 0; i < Q; ++i) fout[i * N + n] = fin[i * N + n];
                     continue;
                 }
-                double f[27];
+                double f[27], t_wall[27];
+                double s_wall = 0.0;
                 for (int i = 0; i < Q; ++i) {
+                    t_wall[i] = 0.0;
                     const long long xs = wrap(x - C27[i][0], nx);
                     const long long ys = wrap(y - C27[i][1], ny);
                     const long long zs = wrap(z - C27[i][2], nz);
@@ -365,11 +373,20 @@ int orc_step(int Q, int nx, int ny, int nz, const unsigned char *tags, const orc
                     } else if (ts >= ORC_WALL0 && ts < ORC_WALL0 + ORC_NWALLS) {
                         const double *uw = p->wall_u[ts - ORC_WALL0];
                         const double cu = C27[i][0] * uw[0] + C27[i][1] * uw[1] + C27[i][2] * uw[2];
-                        f[i] = fin[o * N + n] + 6.0 * weight_of(Q, C27[i]) * p->rho_wall * cu;
+                        t_wall[i] = 6.0 * weight_of(Q, C27[i]) * cu;
+                        s_wall += t_wall[i];
+                        f[i] = fin[o * N + n];
                     } else {
                         f[i] = fin[i * N + s];
                     }
                 }
+                double rho_w = p->rho_wall;
+                if (p->wall_rho_local) {
+                    double rho0 = 0.0;
+                    for (int i = 0; i < Q; ++i) rho0 += f[i];
+                    rho_w = rho0 / (1.0 - s_wall);
+                }
+                for (int i = 0; i < Q; ++i) f[i] += rho_w * t_wall[i];
                 double fo[27];
                 if (p->closure == ORC_STREAM_ONLY) {
                     for (int i = 0; i < Q; ++i) fo[i] = f[i];

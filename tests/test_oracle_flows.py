@@ -140,12 +140,13 @@ def test_tgv2d_decay_rate_and_convergence():
     assert 2.5 < err32 / err64 < 6.0
 
 
-def _channel_run(tau, H, g, steps, moving=None):
+def _channel_run(tau, H, g, steps, moving=None, wall_rho_local=False):
     ny = H + 2
     tags = inp.channel_tags(1, ny, 1, moving_top=moving is not None,
                             fluid_tag=oracle.FORCED if g else oracle.FLUID)
     walls = [tuple(moving)] if moving is not None else None
-    prob = oracle.Problem(19, 1, ny, 1, tags, tau=tau, force=(g, 0.0, 0.0), wall_u=walls)
+    prob = oracle.Problem(19, 1, ny, 1, tags, tau=tau, force=(g, 0.0, 0.0), wall_u=walls,
+                          wall_rho_local=wall_rho_local)
     f = prob.init_equilibrium()
     f = prob.step(f, steps)
     _, u = prob.moments(f)
@@ -179,6 +180,65 @@ def test_couette_linear_with_ladd_wall(tau):
     y = np.arange(1, H + 1, dtype=float)
     exact = U * (y - 0.5) / H
     assert np.max(np.abs(ux[1:H + 1] - exact)) <= 1e-9 * U
+
+
+@pytest.mark.parametrize("tau", [0.6, 1.3])
+def test_couette_linear_with_local_density_wall(tau):
+    """A tangential wall moving in its own plane: the wall terms of every
+    node cancel in pairs (s = 0), the density stays 1, and Ladd's wall with
+    the local density gives the same exact linear profile."""
+    H, U = 12, 0.02
+    ux, _, _ = _channel_run(tau, H, 0.0, 15000, moving=(U, 0.0, 0.0), wall_rho_local=True)
+    y = np.arange(1, H + 1, dtype=float)
+    exact = U * (y - 0.5) / H
+    assert np.max(np.abs(ux[1:H + 1] - exact)) <= 1e-9 * U
+
+
+def test_local_wall_density_is_the_node_density():
+    """With the local-density wall, the density used in every wall term is
+    the node's density after streaming.  Brute force on a tiny lattice of
+    random tags and walls moving in all directions: rebuild each fluid node's
+    pulled set from the pre-step state with rho_wall = the node's density
+    after the step (collision conserves mass), and check that the set sums
+    to that density; with rho_wall = 1 it does not."""
+    Q = 19
+    c, w, _ = oracle.lattice(Q)
+    shape = (4, 5, 6)
+    nz, ny, nx = shape
+    tags = inp.random_tags(shape, seed=91, p_solid=0.1, p_forced=0.0, p_wall=0.25, n_walls=2)
+    f0 = 1.04 * inp.random_populations(w, shape, seed=92, amplitude=0.05)
+    walls = [(0.05, -0.03, 0.02), (-0.02, 0.04, 0.06)]
+    opp = [0] + [i + 1 if i % 2 else i - 1 for i in range(1, Q)]
+    checked = 0
+    for local in (True, False):
+        prob = oracle.Problem(Q, nx, ny, nz, tags, tau=0.7, wall_u=walls, wall_rho_local=local)
+        rho1 = prob.step(f0, 1).sum(axis=0)
+        worst = 0.0
+        for z in range(nz):
+            for y in range(ny):
+                for x in range(nx):
+                    if tags[z, y, x] >= oracle.SOLID:
+                        continue
+                    pulled, has_term = 0.0, False
+                    for i in range(Q):
+                        sz, sy, sx = (z - c[i, 2]) % nz, (y - c[i, 1]) % ny, (x - c[i, 0]) % nx
+                        ts = tags[sz, sy, sx]
+                        if ts < oracle.SOLID:
+                            pulled += f0[i, sz, sy, sx]
+                        else:
+                            pulled += f0[opp[i], z, y, x]
+                            if ts >= oracle.WALL0:
+                                uw = walls[ts - oracle.WALL0]
+                                pulled += 6.0 * w[i] * rho1[z, y, x] * float(np.dot(c[i], uw))
+                                has_term = True
+                    if has_term:
+                        worst = max(worst, abs(pulled - rho1[z, y, x]))
+                        checked += local
+        if local:
+            assert worst <= 1e-13
+        else:
+            assert worst > 1e-6
+    assert checked > 20
 
 
 def test_slit_permeability_closed_form():
