@@ -113,7 +113,12 @@ typedef struct {
  *  trt_magic TRT's Lambda = (tau - 1/2)(tau_minus - 1/2) > 0, which sets the
  *           relaxation time tau_minus of the part of the populations that is
  *           odd under i -> opp(i); tau relaxes the even part.  Lambda = 3/16
- *           puts halfway bounce-back walls exactly halfway at any tau. */
+ *           puts halfway bounce-back walls exactly halfway at any tau.
+ *  wall_rho_local  1: rho_wall is each node's own density after streaming
+ *           (rho_wall is then ignored).  The wall terms are linear in it, so
+ *           it is rho0 / (1 - s), with rho0 the node's density with plain
+ *           bounce-back and s the sum of 6 w_i (c_i . wall_u) over its
+ *           moving-wall links.  0 (default): the constant rho_wall. */
 typedef struct {
     double tau;
     double force[3];
@@ -122,6 +127,7 @@ typedef struct {
     double wall_u[LBM_NWALLS][3];
     double rho_wall;
     double trt_magic;
+    int wall_rho_local;
 } lbm_params;
 
 /* Sums over fluid nodes (tags FLUID and FORCED), accumulated in FP64 from

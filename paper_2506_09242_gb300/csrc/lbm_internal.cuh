@@ -128,7 +128,8 @@ template <typename T> struct KParams {
     T tau;                        // tau
     T force[3];                   // g
     T smag18;                     // 18 Cs^2
-    T wall6[LBM_NWALLS][3];       // 6 rho_wall u_wall (Ladd term = w_i c_i . wall6)
+    T wall6[LBM_NWALLS][3];       // 6 rho_wall u_wall (Ladd term = w_i c_i . wall6); 6 u_wall when wall_local
+    int wall_local;               // rho_wall = the node's density after streaming
 };
 
 // Number of FP64 slots of one reduction partial.

@@ -24,8 +24,10 @@ template <typename T> inline KParams<T> make_kparams(int Q, const lbm_params &p)
     k.omega_minus = p.trt_magic > 0.0 ? (T)(1.0 / (0.5 + p.trt_magic / (p.tau - 0.5))) : k.omega;
     for (int a = 0; a < 3; ++a) k.force[a] = (T)p.force[a];
     k.smag18 = (T)(18.0 * p.cs_smag * p.cs_smag);
+    k.wall_local = p.wall_rho_local != 0;
+    const double rw = k.wall_local ? 1.0 : p.rho_wall;
     for (int w = 0; w < LBM_NWALLS; ++w)
-        for (int a = 0; a < 3; ++a) k.wall6[w][a] = (T)(6.0 * p.rho_wall * p.wall_u[w][a]);
+        for (int a = 0; a < 3; ++a) k.wall6[w][a] = (T)(6.0 * rw * p.wall_u[w][a]);
     return k;
 }
 
@@ -320,8 +322,37 @@ __device__ __forceinline__ long long linear_block() { return blockIdx.x + (long 
 // Where the bounced value sits depends on the pattern: AB reads it from
 // A[opp(i)][x], the odd AA step from F[i][x] (layout S), and the even AA step
 // has already read it from F[i][x] (layout P) and only adds the wall term.
-// Returns the links with a SOLID or WALL source (bit i).
+// Returns the links with a SOLID or WALL source (bit i).  With the
+// local-density wall (p.wall_local) the wall terms are added after all links
+// are bounced, scaled by the node's density rho0 / (1 - s).
 // ---------------------------------------------------------------------------
+// Ladd's moving-wall term 6 w_i rho_wall (c_i . u_wall) of the wall whose tag
+// is ts (without rho_wall for the local-density wall).
+template <int Q, typename T>
+__device__ __forceinline__ T wall_term(int i, unsigned ts, const KParams<T> &p)
+{
+    // select the wall's velocity without indexing the parameter block
+    // dynamically (which would copy it to local memory)
+    T ux = T(0), uy = T(0), uz = T(0);
+#pragma unroll
+    for (int k = 0; k < LBM_NWALLS; ++k)
+        if (ts == (unsigned)(LBM_TAG_WALL0 + k)) {
+            ux = p.wall6[k][0];
+            uy = p.wall6[k][1];
+            uz = p.wall6[k][2];
+        }
+    return wgt<T>(Q, i) * (T(cvel(i, 0)) * ux + T(cvel(i, 1)) * uy + T(cvel(i, 2)) * uz);
+}
+
+// The local wall density: rho0 / (1 - s), rho0 = 1 + sum h (plain bounce-back).
+template <int Q, typename T> __device__ __forceinline__ T local_wall_rho(const T (&h)[Q], T s)
+{
+    T r0 = T(1);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) r0 += h[i];
+    return r0 / (T(1) - s);
+}
+
 template <int Q, typename S, int PAT = kPatAB>
 __device__ __forceinline__ uint32_t apply_walls(typename Store<S>::T (&h)[Q], const S *__restrict__ A,
                                                 const uint8_t *__restrict__ tags, const Grid &g, const Nbr &nb,
@@ -329,6 +360,8 @@ __device__ __forceinline__ uint32_t apply_walls(typename Store<S>::T (&h)[Q], co
 {
     using T = typename Store<S>::T;
     uint32_t wall = 0;
+    T s = T(0);
+    bool moving = false;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const unsigned ts = tags[nb.src(i)] & kTagMask;
@@ -338,20 +371,25 @@ __device__ __forceinline__ uint32_t apply_walls(typename Store<S>::T (&h)[Q], co
                   : PAT == kPatAAOdd ? pop_ld<S, PAT>(A + (long long)i * g.sN + nb.self)
                                      : h[i];
             if (ts >= LBM_TAG_WALL0) {
-                // select the wall's velocity without indexing the parameter
-                // block dynamically (which would copy it to local memory)
-                T ux = T(0), uy = T(0), uz = T(0);
-#pragma unroll
-                for (int k = 0; k < LBM_NWALLS; ++k)
-                    if (ts == (unsigned)(LBM_TAG_WALL0 + k)) {
-                        ux = p.wall6[k][0];
-                        uy = p.wall6[k][1];
-                        uz = p.wall6[k][2];
-                    }
-                v += wgt<T>(Q, i) * (T(cvel(i, 0)) * ux + T(cvel(i, 1)) * uy + T(cvel(i, 2)) * uz);
+                const T term = wall_term<Q, T>(i, ts, p);
+                if (p.wall_local) {
+                    s += term;
+                    moving = true;
+                } else {
+                    v += term;
+                }
             }
             h[i] = v;
         }
+    }
+    if (p.wall_local && moving) {
+        const T rw = local_wall_rho<Q, T>(h, s);
+#pragma unroll
+        for (int i = 1; i < Q; ++i)
+            if ((wall >> i) & 1u) {
+                const unsigned ts = tags[nb.src(i)] & kTagMask;
+                if (ts >= LBM_TAG_WALL0) h[i] += rw * wall_term<Q, T>(i, ts, p);
+            }
     }
     return wall;
 }
@@ -579,20 +617,26 @@ __global__ void __launch_bounds__(kStepThreads)
     if constexpr (REDUCE) block_partial_f32(ns, partials + linear_block() * kRedSlots);
 }
 
-// Ladd's moving-wall term 6 w_i rho_wall (c_i . u_wall) of the wall whose tag
-// is ts, selected without dynamic indexing of the parameter block.
+// The local-density wall on compact storage: h holds the bounced links
+// without their wall terms; adds rho0 / (1 - s) times each term.
 template <int Q, typename T>
-__device__ __forceinline__ T wall_term(int i, unsigned ts, const KParams<T> &p)
+__device__ __forceinline__ void compact_local_wall(T (&h)[Q], const int *__restrict__ nbr, long long t, long long nfp,
+                                                   uint32_t m, const KParams<T> &p)
 {
-    T ux = T(0), uy = T(0), uz = T(0);
+    T s = T(0);
 #pragma unroll
-    for (int k = 0; k < LBM_NWALLS; ++k)
-        if (ts == (unsigned)(LBM_TAG_WALL0 + k)) {
-            ux = p.wall6[k][0];
-            uy = p.wall6[k][1];
-            uz = p.wall6[k][2];
+    for (int i = 1; i < Q; ++i)
+        if ((m >> i) & 1u) {
+            const int k = __ldg(nbr + (long long)(i - 1) * nfp + t);
+            if (k < -1) s += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - k), p);
         }
-    return wgt<T>(Q, i) * (T(cvel(i, 0)) * ux + T(cvel(i, 1)) * uy + T(cvel(i, 2)) * uz);
+    const T rw = local_wall_rho<Q, T>(h, s);
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+        if ((m >> i) & 1u) {
+            const int k = __ldg(nbr + (long long)(i - 1) * nfp + t);
+            if (k < -1) h[i] += rw * wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - k), p);
+        }
 }
 
 // ---------------------------------------------------------------------------
@@ -622,12 +666,16 @@ __global__ void __launch_bounds__(kStepThreads)
 #pragma unroll
         for (int i = 0; i < Q; ++i) h[i] = St::ldc(F + (long long)i * nfp + t);
         if (m & kListAnyWall) {
+            if (p.wall_local) {
+                compact_local_wall<Q, T>(h, nbr, t, nfp, m, p);
+            } else {
 #pragma unroll
-            for (int i = 1; i < Q; ++i)
-                if ((m >> i) & 1u) {
-                    const int s = __ldg(nbr + (long long)(i - 1) * nfp + t);
-                    if (s < -1) h[i] += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - s), p);
-                }
+                for (int i = 1; i < Q; ++i)
+                    if ((m >> i) & 1u) {
+                        const int s = __ldg(nbr + (long long)(i - 1) * nfp + t);
+                        if (s < -1) h[i] += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - s), p);
+                    }
+            }
         }
         collide_node<Q, T, CLOSURE>(h, (m & kListForced) != 0u, p);
 #pragma unroll
@@ -647,9 +695,10 @@ __global__ void __launch_bounds__(kStepThreads)
             const long long a = s >= 0 ? (long long)slot * nfp + s
                                        : (long long)(PAT == kPatAB ? opp(i) : i) * nfp + t;
             T v = pop_ld<S, PAT>(F + a);
-            if (s < -1) v += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - s), p);
+            if (s < -1 && !p.wall_local) v += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - s), p);
             h[i] = v;
         }
+        if (p.wall_local && (m & kListAnyWall)) compact_local_wall<Q, T>(h, nbr, t, nfp, m, p);
         collide_node<Q, T, CLOSURE>(h, (m & kListForced) != 0u, p);
         if constexpr (PAT == kPatAB) {
 #pragma unroll

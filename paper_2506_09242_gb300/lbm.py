@@ -52,6 +52,7 @@ class Params(ctypes.Structure):
         ("wall_u", (ctypes.c_double * 3) * NWALLS),
         ("rho_wall", ctypes.c_double),
         ("trt_magic", ctypes.c_double),
+        ("wall_rho_local", ctypes.c_int),
     ]
 
 
@@ -265,7 +266,8 @@ class Lattice:
 
     # -- configuration -------------------------------------------------------
     def set_params(self, tau: float, *, force=(0.0, 0.0, 0.0), closure: int = CLOSURE_BGK, cs_smag: float = 0.0,
-                   wall_u=None, rho_wall: float = 1.0, trt_magic: float = 3.0 / 16.0):
+                   wall_u=None, rho_wall: float = 1.0, trt_magic: float = 3.0 / 16.0,
+                   wall_rho_local: bool = False):
         p = Params()
         p.tau = tau
         for a in range(3):
@@ -278,6 +280,7 @@ class Lattice:
                     p.wall_u[k][a] = v[a]
         p.rho_wall = rho_wall
         p.trt_magic = trt_magic
+        p.wall_rho_local = 1 if wall_rho_local else 0
         self._call("lbm_set_params", ctypes.byref(p))
         self.params = p
 

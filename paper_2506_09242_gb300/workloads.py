@@ -9,8 +9,8 @@
   FP16- and BF16-shifted storage. Records kinetic energy and enstrophy curves
   and the velocity error against the FP64 run at chosen times.
 
-torch is used for device buffers and for differences of fields when
-evaluating errors.
+torch is used for device buffers, for differences of fields when evaluating
+errors and for time averages of velocity fields.
 """
 from __future__ import annotations
 
@@ -115,6 +115,120 @@ def cavity(n: int = 256, *, re: float = 1000.0, u_lid: float = 0.1, steps: int =
             "ux_centreline_z": u[0, :, mid, mid][:: max(1, n // 16)].tolist()}
 
 
+def _cavity_profiles(u, n: int, u_lid: float):
+    """Centreline profiles of the cavity velocity u[3][nz][ny][nx] (numpy):
+    u_x along the vertical centreline and u_z along the horizontal one, over
+    the fluid nodes 1 .. n-2, with positions xi = (k - 0.5) / (n - 2) between
+    the halfway walls."""
+    import numpy as np
+    m = n // 2
+    k = np.arange(1, n - 1)
+    xi = (k - 0.5) / (n - 2)
+    if n % 2:  # odd n: the centreline is a node line
+        ux = u[0, 1:n - 1, m, m]
+        uz = u[2, m, m, 1:n - 1]
+    else:      # even n: average the two node lines around the centre plane
+        ux = 0.25 * (u[0, 1:n - 1, m - 1, m - 1] + u[0, 1:n - 1, m, m - 1] + u[0, 1:n - 1, m - 1, m] + u[0, 1:n - 1, m, m])
+        uz = 0.25 * (u[2, m - 1, m - 1, 1:n - 1] + u[2, m, m - 1, 1:n - 1] + u[2, m - 1, m, 1:n - 1] + u[2, m, m, 1:n - 1])
+    return xi, ux / u_lid, uz / u_lid
+
+
+def cavity_steady(n: int = 256, *, re: float = 1000.0, u_lid: float = 0.1, t_max: float = 80.0,
+                  check_tc: float = 0.5, tol: float = 1e-6, averages=(), dtype: str = "f32") -> dict:
+    """The lid-driven cavity of Sec. 3.2 run for long times.
+
+    The walls are halfway between the SOLID (or lid) nodes and the fluid, so
+    the cavity side is L = n - 2 and nu = u_lid L / Re.  The kinetic energy
+    per fluid node is checked every check_tc convective times t_c = L / u_lid;
+    the run counts as steady once it changes by less than tol (relative) over
+    one t_c.  For each window (t0, t1) in averages the velocity field is also
+    averaged over samples taken every check_tc in [t0, t1] (for unsteady
+    Reynolds numbers; the run then goes on to the last window's end);
+    the centreline profiles of the final and averaged fields are returned.
+    """
+    import numpy as np
+    import torch
+    import lbm_inputs as inp
+    L = n - 2
+    tau = 0.5 + 3.0 * u_lid * L / re
+    tc = L / u_lid
+    hist, t_step, steps, converged = [], 0.0, 0, False
+    means = [[None, 0] for _ in averages]
+    with lbm.Lattice(n, n, n, lbm.D3Q19, dtype) as lat:
+        lat.set_tags(inp.cavity_tags(n))
+        lat.set_params(tau, wall_u=[(u_lid, 0.0, 0.0)])
+        lat.init_equilibrium()
+        n_fluid = int(lat.census()[lbm.TAG_FLUID])
+        uu = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
+        per_check = max(1, int(round(check_tc * tc)))
+        per_tc = int(round(1.0 / check_tc))
+        while steps < t_max * tc:
+            _sync()
+            t0 = time.perf_counter()
+            lat.step(per_check)
+            _sync()
+            t_step += time.perf_counter() - t0
+            steps += per_check
+            ke = lat.reduce()["ke"] / n_fluid
+            hist.append((steps / tc, ke))
+            t = steps / tc
+            inside = [k for k, w in enumerate(averages) if w[0] <= t <= w[1] + 1e-9]
+            if inside:
+                lat.moments(None, uu)
+                for k in inside:
+                    means[k][0] = uu.clone() if means[k][0] is None else means[k][0].add_(uu)
+                    means[k][1] += 1
+            if not averages and len(hist) > per_tc:
+                prev = hist[-1 - per_tc][1]
+                if abs(ke - prev) <= tol * abs(ke):
+                    converged = True
+                    break
+        lat.moments(None, uu)
+        final = uu.cpu().numpy()
+        avgs = [(m / c).cpu().numpy() if c else None for m, c in means]
+        del uu, means
+    torch.cuda.empty_cache()
+    xi, ux, uz = _cavity_profiles(final, n, u_lid)
+    out = {"n": n, "re": re, "u_lid": u_lid, "tau": tau, "L": L, "t_c_steps": tc, "steps": steps,
+           "t_end_tc": steps / tc, "converged": converged, "tol_per_tc": tol,
+           "glups_fluid": n_fluid * steps / t_step / 1e9, "glups_all_nodes": n ** 3 * steps / t_step / 1e9,
+           "ke_history": hist[:: max(1, len(hist) // 40)] + hist[-3:],
+           "profile": {"xi": xi.tolist(), "ux_vertical": ux.tolist(), "uz_horizontal": uz.tolist()}}
+    out["averages"] = []
+    for w, avg in zip(averages, avgs):
+        if avg is None:
+            continue
+        _, ua, za = _cavity_profiles(avg, n, u_lid)
+        out["averages"].append({"window_tc": list(w), "ux_vertical": ua.tolist(), "uz_horizontal": za.tolist()})
+    return out
+
+
+def cavity_study(sizes=(128, 256), *, re: float = 1000.0, t_max: float = 80.0, re_unsteady: float = 3200.0,
+                 n_unsteady: int = 256, windows=((20.0, 30.0), (30.0, 40.0))) -> dict:
+    """Steady Re = 1000 on two grids (grid convergence of the centreline
+    profiles, coarse positions, the fine profile interpolated), and two
+    time-averaging windows of the unsteady Re = 3200 flow (statistical
+    self-consistency of the averaged profiles)."""
+    import numpy as np
+    runs = {n: cavity_steady(n, re=re, t_max=t_max) for n in sizes}
+    a, b = runs[sizes[0]]["profile"], runs[sizes[-1]]["profile"]
+    dux = np.max(np.abs(np.interp(a["xi"], b["xi"], b["ux_vertical"]) - np.array(a["ux_vertical"])))
+    duz = np.max(np.abs(np.interp(a["xi"], b["xi"], b["uz_horizontal"]) - np.array(a["uz_horizontal"])))
+    out = {"steady": {str(n): {k: v for k, v in r.items() if k != "profile"} for n, r in runs.items()},
+           "profiles": {str(n): r["profile"] for n, r in runs.items()},
+           "grid_difference_max_over_u_lid": {"ux_vertical": float(dux), "uz_horizontal": float(duz)}}
+    if re_unsteady:
+        r = cavity_steady(n_unsteady, re=re_unsteady, t_max=max(w[1] for w in windows), averages=windows)
+        a0, a1 = r["averages"][0], r["averages"][1]
+        d1 = np.max(np.abs(np.array(a0["ux_vertical"]) - np.array(a1["ux_vertical"])))
+        d2 = np.max(np.abs(np.array(a0["uz_horizontal"]) - np.array(a1["uz_horizontal"])))
+        out["unsteady"] = {"re": re_unsteady, "n": n_unsteady, "windows_tc": [list(w) for w in windows],
+                           "window_difference_max_over_u_lid": {"ux_vertical": float(d1), "uz_horizontal": float(d2)},
+                           "ke_history": r["ke_history"], "glups_fluid": r["glups_fluid"],
+                           "averages": r["averages"], "xi": r["profile"]["xi"]}
+    return out
+
+
 def tgv_precision(n: int = 512, Q: int = 27, *, dtypes=("f64", "f32", "f16", "bf16", "f16s"), u0: float = 0.04,
                   re: float = 1600.0, t_end: float = 10.0, every: float = 0.5, error_at=(1.0, 5.0, 10.0)) -> dict:
     """Runs the TGV once per storage type (FP64 first) and compares each
@@ -166,7 +280,7 @@ def tgv_precision(n: int = 512, Q: int = 27, *, dtypes=("f64", "f32", "f16", "bf
 def main(argv=None):  # pragma: no cover - GPU workflow entry point
     import argparse
     ap = argparse.ArgumentParser(description="reference workloads")
-    ap.add_argument("which", choices=["porous", "porous_tau", "cavity", "tgv_precision"])
+    ap.add_argument("which", choices=["porous", "porous_tau", "cavity", "cavity_study", "tgv_precision"])
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--Q", type=int, default=27)
     ap.add_argument("--t-end", type=float, default=10.0)
@@ -178,6 +292,8 @@ def main(argv=None):  # pragma: no cover - GPU workflow entry point
         res = porous_tau_study(a.n or 200)
     elif a.which == "cavity":
         res = cavity(a.n or 256)
+    elif a.which == "cavity_study":
+        res = cavity_study()
     else:
         res = tgv_precision(a.n or 512, a.Q, t_end=a.t_end)
     text = json.dumps(res, indent=1)
