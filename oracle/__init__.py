@@ -99,6 +99,7 @@ def lib():
         _lib.orc_mlp_dtau.argtypes = [P, P, I, P]
         _lib.orc_mlp_dtau.restype = D
         _lib.orc_step.argtypes = [I, I, I, I, P, ctypes.POINTER(Params), P, P]
+        _lib.orc_closure_features.argtypes = [I, I, I, I, P, ctypes.POINTER(Params), P, P]
         _lib.orc_init_equilibrium.argtypes = [I, I, I, I, P, P, P]
         _lib.orc_moments.argtypes = [I, I, I, I, P, ctypes.POINTER(Params), P, P, P]
         _lib.orc_reduce.argtypes = [I, I, I, I, P, ctypes.POINTER(Params), P, ctypes.POINTER(Reduction)]
@@ -203,6 +204,18 @@ class Problem:
                 raise ValueError("oracle step rejected its arguments")
             a, b = b, a
         return a
+
+    def closure_features(self, f: np.ndarray) -> np.ndarray:
+        """Inputs of the learned closure for the step that would follow f:
+        (Pi^neq xx, yy, zz, xy, xz, yz, rho) of each node's pulled set, shape
+        (nz, ny, nx, 7), zeros on solid and wall nodes."""
+        x = np.zeros(self.shape + (7,))
+        ff = _f64(f)
+        rc = lib().orc_closure_features(self.Q, self.nx, self.ny, self.nz, _ptr(self.tags), ctypes.byref(self.p),
+                                        _ptr(ff), _ptr(x))
+        if rc != 0:
+            raise ValueError("oracle closure features rejected their arguments")
+        return x
 
     def moments(self, f: np.ndarray):
         rho = np.zeros(self.shape)

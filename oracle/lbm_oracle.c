@@ -270,6 +270,23 @@ double orc_mlp_dtau(const double *P, const double *norm, int bf16, const double 
     return norm[2 * ORC_MLP_IN] * softplus(y);
 }
 
+/* Non-equilibrium stress Pi_ab = sum_i c_ia c_ib (f_i - feq_i), components
+ * (xx, yy, zz, xy, xz, yz). */
+static void nonequilibrium_stress(int Q, const double *f, const double *feq, double *pi6)
+{
+    for (int k = 0; k < 6; ++k) pi6[k] = 0.0;
+    for (int i = 0; i < Q; ++i) {
+        double d = f[i] - feq[i];
+        const int *c = C27[i];
+        pi6[0] += c[0] * c[0] * d;
+        pi6[1] += c[1] * c[1] * d;
+        pi6[2] += c[2] * c[2] * d;
+        pi6[3] += c[0] * c[1] * d;
+        pi6[4] += c[0] * c[2] * d;
+        pi6[5] += c[1] * c[2] * d;
+    }
+}
+
 /* --- One cell's collision (Sec. 3.1 BGK, Guo force, closures). ---------- */
 static void collide(int Q, const orc_params *p, int forced, const double *f, double *fout)
 {
@@ -290,18 +307,8 @@ static void collide(int Q, const orc_params *p, int forced, const double *f, dou
 
     double tau = p->tau;
     if (p->closure == ORC_SMAGORINSKY || p->closure == ORC_MLP) {
-        /* Non-equilibrium stress Pi_ab = sum_i c_ia c_ib (f_i - feq_i). */
-        double pi6[6] = {0, 0, 0, 0, 0, 0};
-        for (int i = 0; i < Q; ++i) {
-            double d = f[i] - feq[i];
-            const int *c = C27[i];
-            pi6[0] += c[0] * c[0] * d;
-            pi6[1] += c[1] * c[1] * d;
-            pi6[2] += c[2] * c[2] * d;
-            pi6[3] += c[0] * c[1] * d;
-            pi6[4] += c[0] * c[2] * d;
-            pi6[5] += c[1] * c[2] * d;
-        }
+        double pi6[6];
+        nonequilibrium_stress(Q, f, feq, pi6);
         if (p->closure == ORC_SMAGORINSKY) {
             tau = orc_tau_smagorinsky(p->tau, p->cs_smag, rho, pi6);
         } else {
@@ -330,18 +337,54 @@ static void collide(int Q, const orc_params *p, int forced, const double *f, dou
 
 static long long wrap(long long a, long long n) { return ((a % n) + n) % n; }
 
-/* One collide-and-stream step in pull form (Sec. 2.3.1-2.3.2):
- *   for every fluid node x and direction i, the pre-collision value is
+/* The pulled (pre-collision) set of fluid node (x, y, z), Sec. 2.3.1-2.3.2:
  *   f_i(x) = f*_i(x - c_i) if the source node is fluid,
  *          = f*_{opp i}(x)                                    if it is SOLID,
  *          = f*_{opp i}(x) + 6 w_i rho_wall (c_i . u_wall_k)   if it is WALL_k,
- *   after which the node collides and its post-collision set is written to
- *   fout.  Solid and wall nodes are not updated (fout = fin there).
- *   With wall_rho_local, rho_wall is the node's own density after this
- *   streaming, rho = sum_i f_i(x).  The wall terms are linear in it:
- *   rho = rho0 + rho s, with rho0 the sum without them and s the sum of
- *   6 w_i (c_i . u_wall_k) over the node's wall links, so
- *   rho = rho0 / (1 - s). */
+ * with rho_wall = p->rho_wall, or, with wall_rho_local, the node's own
+ * density after streaming, rho = sum_i f_i(x).  The wall terms are linear in
+ * it: rho = rho0 + rho s, with rho0 the sum without them and s the sum of
+ * 6 w_i (c_i . u_wall_k) over the node's wall links, so rho = rho0 / (1 - s). */
+static void pull_node(int Q, long long nx, long long ny, long long nz, const unsigned char *tags, const orc_params *p,
+                      const double *fin, long long x, long long y, long long z, double *f)
+{
+    const long long N = nx * ny * nz;
+    const long long n = x + nx * (y + ny * z);
+    double t_wall[27];
+    double s_wall = 0.0;
+    for (int i = 0; i < Q; ++i) {
+        t_wall[i] = 0.0;
+        const long long xs = wrap(x - C27[i][0], nx);
+        const long long ys = wrap(y - C27[i][1], ny);
+        const long long zs = wrap(z - C27[i][2], nz);
+        const long long s = xs + nx * (ys + ny * zs);
+        const unsigned char ts = tags ? tags[s] : ORC_FLUID;
+        const int o = opposite_of(Q, i);
+        if (ts == ORC_SOLID) {
+            f[i] = fin[o * N + n];
+        } else if (ts >= ORC_WALL0 && ts < ORC_WALL0 + ORC_NWALLS) {
+            const double *uw = p->wall_u[ts - ORC_WALL0];
+            const double cu = C27[i][0] * uw[0] + C27[i][1] * uw[1] + C27[i][2] * uw[2];
+            t_wall[i] = 6.0 * weight_of(Q, C27[i]) * cu;
+            s_wall += t_wall[i];
+            f[i] = fin[o * N + n];
+        } else {
+            f[i] = fin[i * N + s];
+        }
+    }
+    double rho_w = p->rho_wall;
+    if (p->wall_rho_local) {
+        double rho0 = 0.0;
+        for (int i = 0; i < Q; ++i) rho0 += f[i];
+        rho_w = rho0 / (1.0 - s_wall);
+    }
+    for (int i = 0; i < Q; ++i) f[i] += rho_w * t_wall[i];
+}
+
+/* One collide-and-stream step in pull form (Sec. 2.3.1-2.3.2): every fluid
+ * node pulls its pre-collision set (pull_node), collides, and its
+ * post-collision set is written to fout.  Solid and wall nodes are not
+ * updated (fout = fin there). */
 int orc_step(int Q, int nx, int ny, int nz, const unsigned char *tags, const orc_params *p, const double *fin,
              double *fout)
 {
@@ -358,35 +401,8 @@ int orc_step(int Q, int nx, int ny, int nz, const unsigned char *tags, const orc
                     for (int i = 0; i < Q; ++i) fout[i * N + n] = fin[i * N + n];
                     continue;
                 }
-                double f[27], t_wall[27];
-                double s_wall = 0.0;
-                for (int i = 0; i < Q; ++i) {
-                    t_wall[i] = 0.0;
-                    const long long xs = wrap(x - C27[i][0], nx);
-                    const long long ys = wrap(y - C27[i][1], ny);
-                    const long long zs = wrap(z - C27[i][2], nz);
-                    const long long s = xs + nx * (ys + ny * zs);
-                    const unsigned char ts = tags ? tags[s] : ORC_FLUID;
-                    const int o = opposite_of(Q, i);
-                    if (ts == ORC_SOLID) {
-                        f[i] = fin[o * N + n];
-                    } else if (ts >= ORC_WALL0 && ts < ORC_WALL0 + ORC_NWALLS) {
-                        const double *uw = p->wall_u[ts - ORC_WALL0];
-                        const double cu = C27[i][0] * uw[0] + C27[i][1] * uw[1] + C27[i][2] * uw[2];
-                        t_wall[i] = 6.0 * weight_of(Q, C27[i]) * cu;
-                        s_wall += t_wall[i];
-                        f[i] = fin[o * N + n];
-                    } else {
-                        f[i] = fin[i * N + s];
-                    }
-                }
-                double rho_w = p->rho_wall;
-                if (p->wall_rho_local) {
-                    double rho0 = 0.0;
-                    for (int i = 0; i < Q; ++i) rho0 += f[i];
-                    rho_w = rho0 / (1.0 - s_wall);
-                }
-                for (int i = 0; i < Q; ++i) f[i] += rho_w * t_wall[i];
+                double f[27];
+                pull_node(Q, nx, ny, nz, tags, p, fin, x, y, z, f);
                 double fo[27];
                 if (p->closure == ORC_STREAM_ONLY) {
                     for (int i = 0; i < Q; ++i) fo[i] = f[i];
@@ -394,6 +410,38 @@ int orc_step(int Q, int nx, int ny, int nz, const unsigned char *tags, const orc
                     collide(Q, p, t == ORC_FORCED, f, fo);
                 }
                 for (int i = 0; i < Q; ++i) fout[i * N + n] = fo[i];
+            }
+    return 0;
+}
+
+/* Closure features of every node for the step that would follow: the
+ * pulled set's non-equilibrium stress Pi^neq (xx, yy, zz, xy, xz, yz) and
+ * density rho, with u from the pulled set (Guo's half-force shift on forced
+ * nodes), x[n][7] for node n = x + nx (y + ny z); zeros on solid and wall
+ * nodes.  These are the inputs of the learned closure (see orc_mlp_dtau). */
+int orc_closure_features(int Q, int nx, int ny, int nz, const unsigned char *tags, const orc_params *p,
+                         const double *fin, double *xout)
+{
+    if (Q != 19 && Q != 27) return -1;
+    for (long long z = 0; z < nz; ++z)
+        for (long long y = 0; y < ny; ++y)
+            for (long long x = 0; x < nx; ++x) {
+                const long long n = x + (long long)nx * (y + (long long)ny * z);
+                const unsigned char t = tags ? tags[n] : ORC_FLUID;
+                double *out = xout + 7 * n;
+                for (int k = 0; k < 7; ++k) out[k] = 0.0;
+                if (is_wall_or_solid(t)) continue;
+                double f[27], feq[27], u[3], j[3] = {0.0, 0.0, 0.0}, rho = 0.0;
+                pull_node(Q, nx, ny, nz, tags, p, fin, x, y, z, f);
+                for (int i = 0; i < Q; ++i) {
+                    rho += f[i];
+                    for (int a = 0; a < 3; ++a) j[a] += C27[i][a] * f[i];
+                }
+                for (int a = 0; a < 3; ++a)
+                    u[a] = (j[a] + (t == ORC_FORCED ? 0.5 * rho * p->force[a] : 0.0)) / rho;
+                orc_equilibrium(Q, rho, u, feq);
+                nonequilibrium_stress(Q, f, feq, out);
+                out[6] = rho;
             }
     return 0;
 }

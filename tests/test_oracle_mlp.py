@@ -107,3 +107,55 @@ def test_c_oracle_network_matches_numpy(bf):
     ref, _ = mlp.forward(P, norm, X, bf=bf)
     got = np.array([oracle.mlp_dtau(P, norm, x, bf16=bf) for x in X])
     assert np.allclose(got, ref, rtol=1e-12, atol=0)
+
+
+def test_closure_features_recomputed_from_the_pulled_set():
+    """The closure inputs of a state are the non-equilibrium stress and the
+    density of each node's pulled set: recomputed here from a stream-only
+    step (which returns the pulled sets) with the equilibrium of their own
+    moments, on random tags, walls and forced nodes."""
+    Q = 19
+    c, w, _ = oracle.lattice(Q)
+    shape = (4, 5, 6)
+    nz, ny, nx = shape
+    tags = inp.random_tags(shape, seed=95, p_solid=0.15, p_forced=0.3, p_wall=0.1, n_walls=2)
+    f = inp.random_populations(w, shape, seed=96, amplitude=0.05)
+    params = dict(force=(1e-3, -2e-3, 5e-4), wall_u=[(0.02, 0.0, -0.01), (0.0, 0.03, 0.01)])
+    feats = oracle.Problem(Q, nx, ny, nz, tags, tau=0.8, **params).closure_features(f)
+    pulled = oracle.Problem(Q, nx, ny, nz, tags, tau=0.8, closure=oracle.STREAM_ONLY, **params).step(f, 1)
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                if tags[z, y, x] >= oracle.SOLID:
+                    assert np.all(feats[z, y, x] == 0.0)
+                    continue
+                p = pulled[:, z, y, x]
+                rho = p.sum()
+                g = np.array(params["force"]) if tags[z, y, x] == oracle.FORCED else np.zeros(3)
+                u = (c.T @ p + 0.5 * rho * g) / rho
+                d = p - oracle.equilibrium(Q, rho, u)
+                pi = [np.sum(c[:, a] * c[:, b] * d) for a, b in ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))]
+                np.testing.assert_allclose(feats[z, y, x, :6], pi, rtol=0, atol=1e-15)
+                assert feats[z, y, x, 6] == pytest.approx(rho, rel=1e-15)
+
+
+def test_closure_features_closed_forms():
+    """A uniform equilibrium has no non-equilibrium stress; steady plane
+    Couette flow has the Chapman-Enskog shear stress
+    Pi_xy = -2 rho c_s^2 tau S_xy = -rho tau U / (3 H)."""
+    Q = 19
+    n = 6
+    rho = np.full((n, n, n), 1.02)
+    u = np.zeros((3, n, n, n))
+    u[0], u[1], u[2] = 0.03, -0.01, 0.02
+    prob = oracle.Problem(Q, n, n, n, tau=0.9)
+    feats = prob.closure_features(prob.init_equilibrium(rho, u))
+    assert np.max(np.abs(feats[..., :6])) <= 1e-16
+    assert np.allclose(feats[..., 6], 1.02, rtol=1e-15)
+    H, U, tau = 12, 0.02, 0.9
+    ny = H + 2
+    tags = inp.channel_tags(1, ny, 1, moving_top=True, fluid_tag=oracle.FLUID)
+    ch = oracle.Problem(Q, 1, ny, 1, tags, tau=tau, wall_u=[(U, 0.0, 0.0)])
+    f = ch.step(ch.init_equilibrium(), 15000)
+    pxy = ch.closure_features(f)[0, 2:H, 0, 3]
+    np.testing.assert_allclose(pxy, -tau * U / (3.0 * H), rtol=2e-3)
