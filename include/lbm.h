@@ -298,6 +298,16 @@ lbm_status lbm_enstrophy(lbm_ctx *ctx, double *out);
  * returns LBM_ERR_STATE. */
 lbm_status lbm_set_closure_weights(lbm_ctx *ctx, const float *params, const float *norm, int on_device);
 
+/* The closure's inputs for the step that would follow the current state,
+ * computed as that step computes them (pull with the boundary rules, in the
+ * context's streaming pattern): x[n][7] = (Pi^neq xx, yy, zz, xy, xz, yz,
+ * rho) of node n = x + nx (y + ny z), FP32, zeros on solid and wall nodes.
+ * The state is not changed.  Training on these a-posteriori features pairs
+ * the network with the inputs the solver really produces.  x is caller-owned
+ * host memory (N * 7 floats) or device memory (on_device).  Synchronizes.
+ * Errors: ARG, OOM, CUDA. */
+lbm_status lbm_closure_features(lbm_ctx *ctx, float *x, int on_device);
+
 /* dtau[n] for features x[n][7] with the collide kernel's tensor-core tile.
  * All pointers are device memory; asynchronous on stream.  Errors: ARG,
  * CUDA (launch). */

@@ -27,6 +27,10 @@ Workflow (no counterpart in the paper; the TGV set-up is Sec. 3.1's):
    learned closure, or the calibrated one. Each is judged by the relative
    L2 error of its dissipation rate -dk/dt against that of the box-filtered
    fine run, where k = <|u|^2 / 2> (Sec. 3.1).
+5. Optionally (a posteriori), a second round trains on inputs taken from
+   the coarse solver's own populations (lbm_closure_features), recorded
+   with the calibrated network in the loop and paired with the filtered
+   fine targets at the same times.
 """
 from __future__ import annotations
 
@@ -60,6 +64,7 @@ class FineRun:
     k_filtered: np.ndarray     # k of the box-filtered velocity
     X: object = None           # training features (torch, device)
     y: object = None           # training targets (torch, device)
+    y_fields: list = field(default_factory=list)  # (t, full coarse target field) per sample time
     glups: float = 0.0
     diverged_at: float | None = None
 
@@ -88,7 +93,7 @@ def fine_run(n: int, re: float, factor: int, *, t_end: float = 10.0, k_every: fl
     spt = steps_per_tc(n)
     n_k = int(round(t_end / k_every))
     every = max(1, int(round(sample_every / k_every)))
-    times, ks, Xs, ys = [], [], [], []
+    times, ks, Xs, ys, y_fields = [], [], [], [], []
     done, t_step = 0, 0.0
     diverged = None
     for j in range(n_k + 1):
@@ -113,9 +118,11 @@ def fine_run(n: int, re: float, factor: int, *, t_end: float = 10.0, k_every: fl
                                 device="cuda")
             Xs.append(X[idx])
             ys.append(y[idx])
+            y_fields.append((j * k_every, y))
     lat.close()
     run = FineRun(re, n, factor, np.array(times), np.array(ks), diverged_at=diverged)
     run.glups = n ** 3 * done / max(t_step, 1e-9) / 1e9
+    run.y_fields = y_fields
     if Xs:
         run.X = torch.cat(Xs)
         run.y = torch.cat(ys)
@@ -129,16 +136,21 @@ class Trained:
     losses: list = field(default_factory=list)
 
 
-def train(X, y, *, steps: int = 2000, batch: int = 8192, lr: float = 2e-3, seed: int = 0) -> Trained:
+def train(X, y, *, steps: int = 2000, batch: int = 8192, lr: float = 2e-3, seed: int = 0,
+          init: Trained | None = None) -> Trained:
     """Adam on minibatches; normalisation from the sample statistics and an
-    output scale that makes y = 0 predict the mean target."""
+    output scale that makes y = 0 predict the mean target.  With init, the
+    network continues from init's weights (normalisation recomputed)."""
     import torch
     import lbm_inputs as inp
     mean = X.mean(dim=0)
     std = X.std(dim=0).clamp_min(1e-12)
     scale = float(y.mean()) / math.log(2.0) if float(y.mean()) > 0 else 1e-6
     norm = torch.cat([mean, std, torch.tensor([scale, 0.0], device="cuda")]).float().contiguous()
-    P = torch.from_numpy(inp.mlp_init(seed).astype(np.float32)).cuda()
+    if init is not None:
+        P = init.params.clone()
+    else:
+        P = torch.from_numpy(inp.mlp_init(seed).astype(np.float32)).cuda()
     m = torch.zeros_like(P)
     v = torch.zeros_like(P)
     gen = torch.Generator(device="cuda")
@@ -196,6 +208,43 @@ def coarse_run(n: int, re: float, closure: str, trained: Trained | None = None, 
     return CoarseRun(closure, np.array(times), np.array(ks), n ** 3 * done / max(t_step, 1e-9) / 1e9, diverged)
 
 
+def solver_samples(n: int, re: float, fine: FineRun, closure: str, trained: Trained | None = None, *,
+                   samples_per_snapshot: int = 200_000, seed: int = 0, cs: float = 0.1):
+    """A-posteriori training pairs: a coarse run (closure in the loop, from
+    the coarse TGV initial field) records its own closure inputs
+    (lbm_closure_features) at the fine run's sample times; each is paired
+    with the filtered fine run's target field at the same time.  Stops early
+    if the coarse run turns unstable."""
+    import torch
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    lat = lbm.Lattice(n, n, n, lbm.D3Q19, "f32")
+    kind = {"bgk": lbm.CLOSURE_BGK, "smagorinsky": lbm.CLOSURE_SMAGORINSKY, "mlp": lbm.CLOSURE_MLP}[closure]
+    lat.set_params(tgv_tau(n, re), closure=kind, cs_smag=cs)
+    if kind == lbm.CLOSURE_MLP:
+        lat.set_closure_weights(trained.params, trained.norm)
+    rho, u = _tgv_fields(n)
+    lat.init_equilibrium(rho, u)
+    spt = steps_per_tc(n)
+    Xs, ys, done = [], [], 0
+    X = torch.empty((n ** 3, 7), dtype=torch.float32, device="cuda")
+    for t, y in fine.y_fields:
+        target = int(round(t * spt))
+        if target > done:
+            lat.step(target - done)
+            done = target
+        try:
+            lat.reduce()
+        except lbm.UnstableError:
+            break
+        lat.closure_features(X)
+        idx = torch.randint(0, n ** 3, (min(samples_per_snapshot, n ** 3),), generator=gen, device="cuda")
+        Xs.append(X[idx])
+        ys.append(y[idx])
+    lat.close()
+    return torch.cat(Xs), torch.cat(ys)
+
+
 def scaled(trained: Trained, alpha: float) -> Trained:
     """The same network with its output (dtau) multiplied by alpha."""
     norm = trained.norm.clone()
@@ -228,9 +277,16 @@ def dissipation_error(fine: FineRun, coarse: CoarseRun) -> float:
 
 
 def experiment(n_fine: int, factor: int, train_re, test_re: float, *, t_end: float = 10.0, steps: int = 2000,
-               batch: int = 8192, samples_per_snapshot: int = 200_000, seed: int = 0) -> dict:
+               batch: int = 8192, samples_per_snapshot: int = 200_000, seed: int = 0,
+               a_posteriori: bool = False) -> dict:
     """Fine runs at train_re (and test_re), training, and the three coarse
-    runs at test_re; returns a JSON-able summary."""
+    runs at test_re; returns a JSON-able summary.
+
+    a_posteriori: a second round trains on the coarse solver's own inputs.
+    The calibrated first-round network runs in the loop of coarse runs at
+    the training Reynolds numbers (solver_samples), the network continues
+    from its first-round weights on those pairs, is recalibrated, and is
+    judged at test_re like the first round."""
     import torch
     n_c = n_fine // factor
     fines = {}
@@ -246,6 +302,20 @@ def experiment(n_fine: int, factor: int, train_re, test_re: float, *, t_end: flo
     runs = {c: coarse_run(n_c, test_re, c, trained, t_end=t_end) for c in ("bgk", "smagorinsky", "mlp")}
     alpha, table = calibrate(trained, n_c, fines, train_re, t_end=t_end)
     runs["mlp_calibrated"] = coarse_run(n_c, test_re, "mlp", scaled(trained, alpha), t_end=t_end)
+    second = {}
+    if a_posteriori:
+        pairs = [solver_samples(n_c, re, fines[re], "mlp", scaled(trained, alpha),
+                                samples_per_snapshot=samples_per_snapshot, seed=seed + 7 + int(re)) for re in train_re]
+        Xa = torch.cat([p[0] for p in pairs])
+        ya = torch.cat([p[1] for p in pairs])
+        trained2 = train(Xa, ya, steps=steps, batch=batch, seed=seed + 3, init=trained)
+        alpha2, table2 = calibrate(trained2, n_c, fines, train_re, t_end=t_end)
+        runs["mlp_a_posteriori"] = coarse_run(n_c, test_re, "mlp", trained2, t_end=t_end)
+        runs["mlp_a_posteriori_calibrated"] = coarse_run(n_c, test_re, "mlp", scaled(trained2, alpha2), t_end=t_end)
+        second = {"a_posteriori": {"samples": int(Xa.shape[0]), "alpha": alpha2,
+                                   "mean_train_error": {str(a): e for a, e in table2.items()},
+                                   "loss_first_last": [trained2.losses[0][1], trained2.losses[-1][1]],
+                                   "feature_std_ce": X.std(dim=0).tolist(), "feature_std_solver": Xa.std(dim=0).tolist()}}
     ref = fines[test_re]
     return {
         "n_fine": n_fine, "n_coarse": n_c, "factor": factor, "train_re": list(train_re), "test_re": test_re,
@@ -257,6 +327,7 @@ def experiment(n_fine: int, factor: int, train_re, test_re: float, *, t_end: flo
         "calibration": {"alpha": alpha, "mean_train_error": {str(a): e for a, e in table.items()}},
         "coarse": {c: {"dissipation_rel_l2": dissipation_error(ref, r), "glups": r.glups,
                        "diverged_at_tc": r.diverged_at} for c, r in runs.items()},
+        **second,
     }
 
 
@@ -268,10 +339,11 @@ def main(argv=None):  # pragma: no cover - GPU workflow entry point
     ap.add_argument("--t-end", type=float, default=10.0)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--held-out", action="store_true", help="train on Re 800 and 3200, test on 1600")
+    ap.add_argument("--a-posteriori", action="store_true", help="second round on the coarse solver's own inputs")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     train_re = (800.0, 3200.0) if a.held_out else (800.0, 1600.0, 3200.0)
-    res = experiment(a.n_fine, a.factor, train_re, 1600.0, t_end=a.t_end, steps=a.steps)
+    res = experiment(a.n_fine, a.factor, train_re, 1600.0, t_end=a.t_end, steps=a.steps, a_posteriori=a.a_posteriori)
     text = json.dumps(res, indent=1)
     print(text)
     if a.out:

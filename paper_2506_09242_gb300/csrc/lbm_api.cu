@@ -887,6 +887,24 @@ lbm_status lbm_reduce(lbm_ctx *ctx, lbm_reduction *out)
     return fill_reduction(ctx, r, out);
 }
 
+lbm_status lbm_closure_features(lbm_ctx *ctx, float *x, int on_device)
+{
+    if (!ctx || !x) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    ENSURE_DENSE(ctx);
+    const size_t nb = sizeof(float) * 7 * (size_t)ctx->g.N;
+    Tmp t(ctx, on_device ? 0 : nb);
+    if (!on_device && !t.p) return fail(ctx, LBM_ERR_OOM, "staging allocation failed");
+    Launch L = make_launch(ctx);
+    float *dst = on_device ? x : (float *)t.p;
+    CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
+                 using S = std::remove_pointer_t<decltype(tag)>;
+                 return launch_closure_features<S>(L, ctx->params, dst);
+             }),
+             "closure features");
+    if (!on_device) CUDA_TRY(ctx, cudaMemcpyAsync(x, t.p, nb, cudaMemcpyDeviceToHost, ctx->stream), "features copy");
+    return sync(ctx);
+}
+
 lbm_status lbm_sync(lbm_ctx *ctx, int timeout_ms)
 {
     if (!ctx) return fail(ctx, LBM_ERR_ARG, "NULL context");

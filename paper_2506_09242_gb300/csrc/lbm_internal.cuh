@@ -186,6 +186,9 @@ template <typename S>
 cudaError_t launch_reduce_aa(const Launch &L, const lbm_params &p, double *partials, int nblocks, double *out);
 template <typename S> cudaError_t launch_moments_aa(const Launch &L, const lbm_params &p, double *rho, double *u);
 template <typename S> cudaError_t launch_get_pop_aa(const Launch &L, int i, double *f_plane);
+// The learned closure's inputs of every node for the next step, x[N][7].
+template <typename S> cudaError_t launch_closure_features(const Launch &L, const lbm_params &p, float *x);
+template <typename S> cudaError_t launch_closure_features_aa(const Launch &L, const lbm_params &p, float *x);
 template <typename S> cudaError_t launch_set_pop(const Launch &L, int i, const double *f_plane);
 
 // Storage-type independent kernels (lbm_api.cu).

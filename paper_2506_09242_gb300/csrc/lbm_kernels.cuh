@@ -1040,6 +1040,44 @@ __global__ void __launch_bounds__(kStepThreads)
 }
 
 // ---------------------------------------------------------------------------
+// The learned closure's inputs for the step that would follow, computed as
+// that step computes them: each node's pulled set (pattern PAT, boundary
+// rules included), its density and non-equilibrium stress;
+// x[n][7] = (Pi xx, yy, zz, xy, xz, yz, rho) for n = x + nx (y + ny z), in
+// FP32; zeros on solid and wall nodes.  Nothing is written to the lattice.
+// ---------------------------------------------------------------------------
+template <int Q, typename S, bool GENERAL, int PAT>
+__global__ void __launch_bounds__(kStepThreads)
+    k_closure_features(const S *__restrict__ A, const uint8_t *__restrict__ tags, Grid g,
+                       KParams<typename Store<S>::T> p, float *__restrict__ xout)
+{
+    using T = typename Store<S>::T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    float *out = xout + 7 * (x + (long long)g.nx * (y + (long long)g.ny * z));
+    Nbr nb;
+    nb.init(g, x, y, z);
+    const unsigned t = GENERAL ? tags[nb.self] : 0u;
+    if (GENERAL && is_wall_tag(t & kTagMask)) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) out[k] = 0.f;
+        return;
+    }
+    T h[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) h[i] = Store<S>::ld(A + step_load_off<PAT>(i, g, nb));
+    if (GENERAL && (t & kNearWall)) apply_walls<Q, S, PAT>(h, A, tags, g, nb, p);
+    const Macro<T> m = node_macros<Q, T>(h, GENERAL && (t & kTagMask) == LBM_TAG_FORCED, p);
+    T pi[6];
+    pi_neq<Q, T>(h, m, pi);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out[k] = (float)pi[k];
+    out[6] = (float)m.rho;
+}
+
+// ---------------------------------------------------------------------------
 // Reduction: FP64 sums over fluid nodes.  Pass 1 writes one partial per block
 // (a fixed grid of at most one resident wave; block b sweeps one contiguous
 // range of the padded node index, its threads side by side), pass 2 adds the
@@ -1375,6 +1413,18 @@ cudaError_t moments_q(const Launch &L, const lbm_params &p, double *rho, double 
     return cudaGetLastError();
 }
 
+template <int Q, typename S, int PAT> cudaError_t features_q(const Launch &L, const lbm_params &p, float *x)
+{
+    dim3 grid, block;
+    node_launch_shape(L.g, grid, block);
+    const auto kp = make_kparams<typename Store<S>::T>(Q, p);
+    if (L.general)
+        k_closure_features<Q, S, true, PAT><<<grid, block, 0, L.stream>>>((const S *)L.A, L.tags, L.g, kp, x);
+    else
+        k_closure_features<Q, S, false, PAT><<<grid, block, 0, L.stream>>>((const S *)L.A, L.tags, L.g, kp, x);
+    return cudaGetLastError();
+}
+
 template <int Q, typename S, int LAY> cudaError_t get_pop_q(const Launch &L, int i, double *f)
 {
     dim3 grid, block;
@@ -1423,6 +1473,11 @@ template <int Q, typename S, int LAY> cudaError_t get_pop_q(const Launch &L, int
         if (L.aa_p) return L.Q == 19 ? moments_q<19, S, kLayP>(L, p, rho, u) : moments_q<27, S, kLayP>(L, p, rho, u); \
         return L.Q == 19 ? moments_q<19, S, kLayS>(L, p, rho, u) : moments_q<27, S, kLayS>(L, p, rho, u);    \
     }                                                                                                        \
+    template <> cudaError_t launch_closure_features_aa<S>(const Launch &L, const lbm_params &p, float *x)     \
+    {                                                                                                        \
+        if (L.aa_p) return L.Q == 19 ? features_q<19, S, kPatAAEven>(L, p, x) : features_q<27, S, kPatAAEven>(L, p, x); \
+        return L.Q == 19 ? features_q<19, S, kPatAAOdd>(L, p, x) : features_q<27, S, kPatAAOdd>(L, p, x);    \
+    }                                                                                                        \
     template <> cudaError_t launch_get_pop_aa<S>(const Launch &L, int i, double *f)                          \
     {                                                                                                        \
         if (L.aa_p) return L.Q == 19 ? get_pop_q<19, S, kLayP>(L, i, f) : get_pop_q<27, S, kLayP>(L, i, f);  \
@@ -1470,6 +1525,11 @@ template <int Q, typename S, int LAY> cudaError_t get_pop_q(const Launch &L, int
         else                                                                                                 \
             k_init<27, S><<<grid, block, 0, L.stream>>>((S *)L.A, (S *)L.B, L.g, rho, u, L.aa);              \
         return cudaGetLastError();                                                                           \
+    }                                                                                                        \
+    template <> cudaError_t launch_closure_features<S>(const Launch &L, const lbm_params &p, float *x)        \
+    {                                                                                                        \
+        if (L.aa) return launch_closure_features_aa<S>(L, p, x);                                             \
+        return L.Q == 19 ? features_q<19, S, kPatAB>(L, p, x) : features_q<27, S, kPatAB>(L, p, x);          \
     }                                                                                                        \
     template <> cudaError_t launch_get_pop<S>(const Launch &L, int i, double *f)                             \
     {                                                                                                        \

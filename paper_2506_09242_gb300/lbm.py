@@ -86,6 +86,7 @@ _P, _I, _D, _LL, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_
 SIGNATURES = {
     "lbm_create": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(Allocator), _P, ctypes.POINTER(_P)]),
     "lbm_create_ex": (_I, [_I, _I, _I, _I, _I, _I, ctypes.POINTER(Allocator), _P, ctypes.POINTER(_P)]),
+    "lbm_closure_features": (_I, [_P, _P, _I]),
     "lbm_destroy": (_I, [_P]),
     "lbm_set_params": (_I, [_P, ctypes.POINTER(Params)]),
     "lbm_set_tags": (_I, [_P, _P, _I]),
@@ -385,6 +386,16 @@ class Lattice:
         if dp != dn:
             raise ValueError("params and norm must both be on the host or both on the device")
         self._call("lbm_set_closure_weights", p, n, dp)
+
+    def closure_features(self, out=None):
+        """The closure's inputs for the next step, (N, 7) FP32 with N in
+        x-fastest node order: a numpy array, or written into the given CUDA
+        tensor (which is returned)."""
+        if out is None:
+            out = np.empty((self.N, 7), dtype=np.float32)
+        p, dev, _keep = _buf(out, np.float32)
+        self._call("lbm_closure_features", p, dev)
+        return out
 
     def info(self) -> dict:
         nbytes, px, q = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()

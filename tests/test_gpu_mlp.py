@@ -154,3 +154,44 @@ def test_mlp_closure_needs_weights():
         assert e.value.status == lbm.ERR_STATE
         with pytest.raises(lbm.LBMError):
             lat.set_closure_weights(np.zeros(1345, np.float32), np.zeros(16, np.float32))  # std = 0
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+@pytest.mark.parametrize("mix", ["dense", "list"])
+def test_closure_features_match_oracle(dtype, pattern, mix):
+    """The closure inputs of the current state (pulled set's stress and
+    density), after odd and even step counts (AA's two layouts), with walls,
+    forcing and compact storage, against the FP64 oracle.  FP64: the FP32
+    rounding of the oracle's values; FP32: within the FP32 cancellation of
+    the stress (1e-8 absolute for h ~ 1e-2)."""
+    Q = 19
+    shape = (6, 7, 40)
+    nz, ny, nx = shape
+    mixes = {"dense": dict(p_solid=0.15, p_forced=0.3, p_wall=0.06),
+             "list": dict(p_solid=0.45, p_forced=0.2, p_wall=0.1)}
+    tags = inp.random_tags(shape, seed=97, n_walls=2, **mixes[mix])
+    walls = [(0.02, 0.0, -0.01), (0.0, 0.03, 0.01)]
+    params = dict(tau=0.7, force=(2e-4, 0.0, -1e-4), wall_u=walls)
+    rho, u = inp.random_velocity_field(shape, seed=98, amplitude=0.05)
+    prob = oracle.Problem(Q, nx, ny, nz, tags, **params)
+    g = prob.init_equilibrium(rho, u)
+    with lbm.Lattice(nx, ny, nz, Q, dtype, pattern=pattern) as lat:
+        lat.set_tags(tags)
+        lat.set_params(**params)
+        lat.init_equilibrium(rho, u)
+        for n in (0, 1, 2):
+            if n:
+                lat.step(n)
+                g = prob.step(g, n)
+            got = lat.closure_features().reshape(nz, ny, nx, 7).astype(np.float64)
+            ref = prob.closure_features(g)
+            if dtype == "f64":
+                assert np.array_equal(got, np.float32(ref).astype(np.float64)) or \
+                    np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-30)) <= 1.2e-7
+            else:
+                assert np.max(np.abs(got[..., :6] - ref[..., :6])) <= 1e-8
+                assert np.max(np.abs(got[..., 6] - ref[..., 6])) <= 1e-6
+            dev = torch.empty((lat.N, 7), dtype=torch.float32, device="cuda")
+            lat.closure_features(dev)
+            assert np.array_equal(dev.cpu().numpy().reshape(nz, ny, nx, 7), got.astype(np.float32))
