@@ -801,7 +801,7 @@ lbm_status lbm_step_reduce(lbm_ctx *ctx, int n, lbm_reduction *out)
     lbm_status st = run_steps(ctx, n - 1, false);
     if (st != LBM_OK) return st;
     Launch L = make_launch(ctx);
-    const long long nparts = fused_partials(L, ctx->elem);
+    const long long nparts = fused_partials(L, ctx->params, ctx->elem);
     if (nparts > ctx->fpart_cap) {
         dev_free(ctx, ctx->fpart, sizeof(float) * kRedSlots * (size_t)ctx->fpart_cap);
         ctx->fpart = (float *)dev_alloc(ctx, sizeof(float) * kRedSlots * (size_t)nparts);

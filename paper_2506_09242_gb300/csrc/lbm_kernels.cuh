@@ -326,6 +326,29 @@ __device__ __forceinline__ long long linear_block() { return blockIdx.x + (long 
 // local-density wall (p.wall_local) the wall terms are added after all links
 // are bounced, scaled by the node's density rho0 / (1 - s).
 // ---------------------------------------------------------------------------
+// c_i . v with only the non-zero terms of c_i (components are 0 or +-1).
+// Written as T(c_x) v_x + T(c_y) v_y + T(c_z) v_z, IEEE semantics would keep
+// every 0 * v_a as a real operation; here the branches fold at compile time
+// once i is a constant of an unrolled loop.
+template <typename T> __device__ __forceinline__ T cdot(int i, T vx, T vy, T vz)
+{
+    const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
+    T r;
+    if (cx) {
+        r = cx > 0 ? vx : -vx;
+        if (cy) r = cy > 0 ? r + vy : r - vy;
+        if (cz) r = cz > 0 ? r + vz : r - vz;
+    } else if (cy) {
+        r = cy > 0 ? vy : -vy;
+        if (cz) r = cz > 0 ? r + vz : r - vz;
+    } else if (cz) {
+        r = cz > 0 ? vz : -vz;
+    } else {
+        r = T(0);
+    }
+    return r;
+}
+
 // Ladd's moving-wall term 6 w_i rho_wall (c_i . u_wall) of the wall whose tag
 // is ts (without rho_wall for the local-density wall).
 template <int Q, typename T>
@@ -341,7 +364,7 @@ __device__ __forceinline__ T wall_term(int i, unsigned ts, const KParams<T> &p)
             uy = p.wall6[k][1];
             uz = p.wall6[k][2];
         }
-    return wgt<T>(Q, i) * (T(cvel(i, 0)) * ux + T(cvel(i, 1)) * uy + T(cvel(i, 2)) * uz);
+    return wgt<T>(Q, i) * cdot<T>(i, ux, uy, uz);
 }
 
 // The local wall density: rho0 / (1 - s), rho0 = 1 + sum h (plain bounce-back).
@@ -353,7 +376,10 @@ template <int Q, typename T> __device__ __forceinline__ T local_wall_rho(const T
     return r0 / (T(1) - s);
 }
 
-template <int Q, typename S, int PAT = kPatAB>
+// LOCAL: the kernel supports the local-density wall (p.wall_local); the
+// 16-bit two-node kernel is built without it (the second pass over the
+// links costs that kernel about 20 registers) and is not used when it is on.
+template <int Q, typename S, int PAT = kPatAB, bool LOCAL = true>
 __device__ __forceinline__ uint32_t apply_walls(typename Store<S>::T (&h)[Q], const S *__restrict__ A,
                                                 const uint8_t *__restrict__ tags, const Grid &g, const Nbr &nb,
                                                 const KParams<typename Store<S>::T> &p)
@@ -372,7 +398,7 @@ __device__ __forceinline__ uint32_t apply_walls(typename Store<S>::T (&h)[Q], co
                                      : h[i];
             if (ts >= LBM_TAG_WALL0) {
                 const T term = wall_term<Q, T>(i, ts, p);
-                if (p.wall_local) {
+                if (LOCAL && p.wall_local) {
                     s += term;
                     moving = true;
                 } else {
@@ -382,7 +408,7 @@ __device__ __forceinline__ uint32_t apply_walls(typename Store<S>::T (&h)[Q], co
             h[i] = v;
         }
     }
-    if (p.wall_local && moving) {
+    if (LOCAL && p.wall_local && moving) {
         const T rw = local_wall_rho<Q, T>(h, s);
 #pragma unroll
         for (int i = 1; i < Q; ++i)
@@ -401,22 +427,48 @@ __device__ __forceinline__ uint32_t apply_walls(typename Store<S>::T (&h)[Q], co
 // moments, the non-equilibrium stress and the relaxation so that the learned
 // closure can run between them.
 // ---------------------------------------------------------------------------
+// sum_i c_ia h_i over the directions with c_ia != 0, in index order, started
+// from the first term (no addition of zero).
+template <int Q, typename T, int AX> __device__ __forceinline__ T csum(const T (&h)[Q])
+{
+    T r = T(0);
+    bool first = true;
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+        if (cvel(i, AX)) {
+            const T v = cvel(i, AX) > 0 ? h[i] : -h[i];
+            r = first ? v : r + v;
+            first = false;
+        }
+    return r;
+}
+
 template <typename T> struct Macro {
     T drho, rho, inv, ux, uy, uz, Gx, Gy, Gz;
 };
 
 // rho = 1 + sum h, j = sum c h (+ rho g / 2 on a forced node), u = j / rho.
-template <int Q, typename T>
+template <int Q, typename T, bool FIRST_TERM = true>
 __device__ __forceinline__ Macro<T> node_macros(const T (&h)[Q], bool forced, const KParams<T> &p)
 {
     Macro<T> m;
-    T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
+    T drho, jx, jy, jz;
+    if constexpr (FIRST_TERM) {
+        drho = h[0];
+        jx = csum<Q, T, 0>(h);
+        jy = csum<Q, T, 1>(h);
+        jz = csum<Q, T, 2>(h);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        drho += h[i];
-        if (cvel(i, 0)) jx += cvel(i, 0) > 0 ? h[i] : -h[i];
-        if (cvel(i, 1)) jy += cvel(i, 1) > 0 ? h[i] : -h[i];
-        if (cvel(i, 2)) jz += cvel(i, 2) > 0 ? h[i] : -h[i];
+        for (int i = 1; i < Q; ++i) drho += h[i];
+    } else {
+        drho = jx = jy = jz = T(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            drho += h[i];
+            if (cvel(i, 0)) jx += cvel(i, 0) > 0 ? h[i] : -h[i];
+            if (cvel(i, 1)) jy += cvel(i, 1) > 0 ? h[i] : -h[i];
+            if (cvel(i, 2)) jz += cvel(i, 2) > 0 ? h[i] : -h[i];
+        }
     }
     m.drho = drho;
     m.rho = T(1) + drho;
@@ -442,16 +494,18 @@ __device__ __forceinline__ Macro<T> node_macros(const T (&h)[Q], bool forced, co
 template <int Q, typename T>
 __device__ __forceinline__ void pi_neq(const T (&h)[Q], const Macro<T> &m, T (&pi)[6])
 {
+    // second moments, each started from its first term (no addition of zero)
     T sxx = T(0), syy = T(0), szz = T(0), sxy = T(0), sxz = T(0), syz = T(0);
+    bool fxx = true, fyy = true, fzz = true, fxy = true, fxz = true, fyz = true;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
-        if (cx) sxx += h[i];
-        if (cy) syy += h[i];
-        if (cz) szz += h[i];
-        if (cx * cy) sxy += cx * cy > 0 ? h[i] : -h[i];
-        if (cx * cz) sxz += cx * cz > 0 ? h[i] : -h[i];
-        if (cy * cz) syz += cy * cz > 0 ? h[i] : -h[i];
+        if (cx) { sxx = fxx ? h[i] : sxx + h[i]; fxx = false; }
+        if (cy) { syy = fyy ? h[i] : syy + h[i]; fyy = false; }
+        if (cz) { szz = fzz ? h[i] : szz + h[i]; fzz = false; }
+        if (cx * cy) { const T v = cx * cy > 0 ? h[i] : -h[i]; sxy = fxy ? v : sxy + v; fxy = false; }
+        if (cx * cz) { const T v = cx * cz > 0 ? h[i] : -h[i]; sxz = fxz ? v : sxz + v; fxz = false; }
+        if (cy * cz) { const T v = cy * cz > 0 ? h[i] : -h[i]; syz = fyz ? v : syz + v; fyz = false; }
     }
     const T d3 = m.drho * (T(1) / T(3));
     pi[0] = sxx - m.rho * m.ux * m.ux - d3;
@@ -462,27 +516,62 @@ __device__ __forceinline__ void pi_neq(const T (&h)[Q], const Macro<T> &m, T (&p
     pi[5] = syz - m.rho * m.uy * m.uz;
 }
 
-// h_i <- h_i + omega (h_eq_i - h_i) + (1 - omega / 2) F_i.
-template <int Q, typename T>
+// h_i <- h_i + omega (h_eq_i - h_i) + (1 - omega / 2) F_i, the rest
+// population first, then each pair of opposite directions (i, i + 1): their
+// equilibria h_eq = S +- A share the even part S = w (drho + rho (4.5 (c.u)^2
+// - 1.5 u^2)) and differ in the sign of the odd part A = 3 w rho (c.u), and
+// Guo's source F = w [3 (c - u) + 9 (c.u) c] . G splits the same way.
+template <int Q, typename T, bool PAIRED = true>
 __device__ __forceinline__ void relax(T (&h)[Q], const Macro<T> &m, T omega, bool forced)
 {
     const T usq15 = T(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
     const T cf = T(1) - T(0.5) * omega;
     const T uG = m.ux * m.Gx + m.uy * m.Gy + m.uz * m.Gz;
+    {
+        const T w0 = wgt<T>(Q, 0);
+        T h0 = h[0] + omega * (w0 * (m.drho - m.rho * usq15) - h[0]);
+        if (forced) h0 += cf * (w0 * (T(-3) * uG));
+        h[0] = h0;
+    }
+    if constexpr (Q == 27 || !PAIRED) {
+        // One direction at a time with the full dot products: the same
+        // algebra as the paired form below.  For D3Q27 the 16-bit two-node
+        // kernel compiles this form to 80 registers (the paired form to
+        // 86-90), which keeps six blocks per SM resident instead of five;
+        // the compact kernel (!PAIRED), bound by the latency of its
+        // gathers, is fastest with it as well (measured).
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
-        const T cu = T(cx) * m.ux + T(cy) * m.uy + T(cz) * m.uz;
-        const T w = wgt<T>(Q, i);
-        // h_eq = f_eq - w = w (drho + rho (3 cu + 4.5 cu^2 - 1.5 u^2))
-        const T heq = w * (m.drho + m.rho * (cu * (T(3) + T(4.5) * cu) - usq15));
-        T hn = h[i] + omega * (heq - h[i]);
-        if (forced) {
-            // Guo: F_i = w [3 (c - u) + 9 (c.u) c] . G
-            const T cG = T(cx) * m.Gx + T(cy) * m.Gy + T(cz) * m.Gz;
-            hn += cf * w * (T(3) * (cG - uG) + T(9) * cu * cG);
+        for (int i = 1; i < Q; ++i) {
+            const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
+            const T cu = T(cx) * m.ux + T(cy) * m.uy + T(cz) * m.uz;
+            const T w = wgt<T>(Q, i);
+            const T heq = w * (m.drho + m.rho * (cu * (T(3) + T(4.5) * cu) - usq15));
+            T hn = h[i] + omega * (heq - h[i]);
+            if (forced) {
+                const T cG = T(cx) * m.Gx + T(cy) * m.Gy + T(cz) * m.Gz;
+                hn += cf * w * (T(3) * (cG - uG) + T(9) * cu * cG);
+            }
+            h[i] = hn;
         }
-        h[i] = hn;
+        return;
+    }
+    const T r3 = T(3) * m.rho;
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const T cu = cdot<T>(i, m.ux, m.uy, m.uz);
+        const T w = wgt<T>(Q, i);
+        const T S = w * (m.drho + m.rho * (T(4.5) * cu * cu - usq15));
+        const T A = (w * r3) * cu;
+        T hi = h[i] + omega * ((S + A) - h[i]);
+        T ho = h[i + 1] + omega * ((S - A) - h[i + 1]);
+        if (forced) {
+            const T cG = cdot<T>(i, m.Gx, m.Gy, m.Gz);
+            const T Fs = w * (T(9) * cu * cG - T(3) * uG), Fa = T(3) * w * cG;
+            hi += cf * (Fs + Fa);
+            ho += cf * (Fs - Fa);
+        }
+        h[i] = hi;
+        h[i + 1] = ho;
     }
 }
 
@@ -504,8 +593,7 @@ __device__ __forceinline__ void relax_trt(T (&h)[Q], const Macro<T> &m, T wp, T 
     }
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
-        const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
-        const T cu = T(cx) * m.ux + T(cy) * m.uy + T(cz) * m.uz;
+        const T cu = cdot<T>(i, m.ux, m.uy, m.uz);
         const T w = wgt<T>(Q, i);
         const T S = w * (m.drho + m.rho * (T(4.5) * cu * cu - usq15));
         const T A = T(3) * w * m.rho * cu;
@@ -513,7 +601,7 @@ __device__ __forceinline__ void relax_trt(T (&h)[Q], const Macro<T> &m, T wp, T 
         const T dm = wm * (T(0.5) * (h[i] - h[i + 1]) - A);
         T hi = h[i] - dp - dm, ho = h[i + 1] - dp + dm;
         if (forced) {
-            const T cG = T(cx) * m.Gx + T(cy) * m.Gy + T(cz) * m.Gz;
+            const T cG = cdot<T>(i, m.Gx, m.Gy, m.Gz);
             const T Fs = w * (T(9) * cu * cG - T(3) * uG), Fa = T(3) * w * cG;
             hi += cfp * Fs + cfm * Fa;
             ho += cfp * Fs - cfm * Fa;
@@ -525,11 +613,17 @@ __device__ __forceinline__ void relax_trt(T (&h)[Q], const Macro<T> &m, T wp, T 
 
 // Returns the density and velocity the collision used (mass and momentum
 // invariants of the new state).
-template <int Q, typename T, int CLOSURE>
+// LEAN selects the paired relaxation and first-term moment sums (fewer
+// instructions, for the issue-bound kernels).  The A/B step on compact
+// storage, bound by the latency of its gathers, takes the one-direction-at-a-
+// time form: 48 registers instead of 64 (28.9 against 20.2 fluid GLUPS on a
+// 400^3 porous medium); its AA steps are faster with the lean form.  The two
+// forms differ only in rounding.
+template <int Q, typename T, int CLOSURE, bool LEAN = true>
 __device__ __forceinline__ Macro<T> collide_node(T (&h)[Q], bool forced, const KParams<T> &p)
 {
     if (CLOSURE == LBM_CLOSURE_STREAM_ONLY) return Macro<T>{};
-    const Macro<T> m = node_macros<Q, T>(h, forced, p);
+    const Macro<T> m = node_macros<Q, T, LEAN>(h, forced, p);
     if (CLOSURE == LBM_CLOSURE_TRT) {
         relax_trt<Q, T>(h, m, p.omega, p.omega_minus, forced);
         return m;
@@ -542,7 +636,7 @@ __device__ __forceinline__ Macro<T> collide_node(T (&h)[Q], bool forced, const K
         const T te = T(0.5) * (p.tau + sqrt(p.tau * p.tau + p.smag18 * sqrt(T(2) * pp) * m.inv));
         omega = T(1) / te;
     }
-    relax<Q, T>(h, m, omega, forced);
+    relax<Q, T, LEAN>(h, m, omega, forced);
     return m;
 }
 
@@ -648,7 +742,10 @@ __device__ __forceinline__ void compact_local_wall(T (&h)[Q], const int *__restr
 // same single load as a streamed one.  (The learned closure needs whole warps
 // of consecutive nodes and keeps the dense sweep.)
 // ---------------------------------------------------------------------------
-template <int Q, typename S, int CLOSURE, int PAT = kPatAB>
+// LOCAL: the local-density wall (p.wall_local); a separate instantiation,
+// since its second pass over the neighbour index keeps the first pass's 18
+// to 26 indices live and costs the kernel 17 to 38 registers.
+template <int Q, typename S, int CLOSURE, int PAT = kPatAB, bool LOCAL = false>
 __global__ void __launch_bounds__(kStepThreads)
     k_collide_stream_compact(const S *__restrict__ A, S *__restrict__ B, const int *__restrict__ nbr,
                              const uint32_t *__restrict__ mask, long long n, long long nfp,
@@ -658,15 +755,30 @@ __global__ void __launch_bounds__(kStepThreads)
     using St = Store<S>;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= n) return;
+    T h[Q];
+    if constexpr (PAT == kPatAB && !LOCAL) {
+        h[0] = St::ld(A + t);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const int s = __ldg(nbr + (long long)(i - 1) * nfp + t);
+            const long long a = s >= 0 ? (long long)i * nfp + s : (long long)opp(i) * nfp + t;
+            T v = St::ld(A + a);
+            if (s < -1) v += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - s), p);
+            h[i] = v;
+        }
+        collide_node<Q, T, CLOSURE, false>(h, (__ldg(mask + t) & kListForced) != 0u, p);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) St::st(B + (long long)i * nfp + t, h[i]);
+        return;
+    }
     const S *F = PAT == kPatAB ? A : B;  // AA: in place through B
     const uint32_t m = __ldg(mask + t);
-    T h[Q];
     if constexpr (PAT == kPatAAEven) {
         // Local reads (layout P); links from a moving wall add Ladd's term.
 #pragma unroll
         for (int i = 0; i < Q; ++i) h[i] = St::ldc(F + (long long)i * nfp + t);
         if (m & kListAnyWall) {
-            if (p.wall_local) {
+            if (LOCAL) {
                 compact_local_wall<Q, T>(h, nbr, t, nfp, m, p);
             } else {
 #pragma unroll
@@ -695,10 +807,10 @@ __global__ void __launch_bounds__(kStepThreads)
             const long long a = s >= 0 ? (long long)slot * nfp + s
                                        : (long long)(PAT == kPatAB ? opp(i) : i) * nfp + t;
             T v = pop_ld<S, PAT>(F + a);
-            if (s < -1 && !p.wall_local) v += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - s), p);
+            if (s < -1 && !LOCAL) v += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - s), p);
             h[i] = v;
         }
-        if (p.wall_local && (m & kListAnyWall)) compact_local_wall<Q, T>(h, nbr, t, nfp, m, p);
+        if (LOCAL && (m & kListAnyWall)) compact_local_wall<Q, T>(h, nbr, t, nfp, m, p);
         collide_node<Q, T, CLOSURE>(h, (m & kListForced) != 0u, p);
         if constexpr (PAT == kPatAB) {
 #pragma unroll
@@ -883,7 +995,7 @@ __device__ __forceinline__ void collide_stream_pair(const S *__restrict__ A, S *
             float t[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) t[i] = h[i].x;
-            apply_walls<Q, S>(t, A, tags, g, nb, p);
+            apply_walls<Q, S, kPatAB, false>(t, A, tags, g, nb, p);
 #pragma unroll
             for (int i = 0; i < Q; ++i) h[i].x = t[i];
         }
@@ -893,7 +1005,7 @@ __device__ __forceinline__ void collide_stream_pair(const S *__restrict__ A, S *
             float t[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) t[i] = h[i].y;
-            apply_walls<Q, S>(t, A, tags, g, nb, p);
+            apply_walls<Q, S, kPatAB, false>(t, A, tags, g, nb, p);
 #pragma unroll
             for (int i = 0; i < Q; ++i) h[i].y = t[i];
         }
@@ -940,9 +1052,9 @@ __device__ __forceinline__ void collide_stream_pair(const S *__restrict__ A, S *
 }
 
 template <int Q, typename S, bool GENERAL, int CLOSURE, bool REDUCE>
-__global__ void __launch_bounds__(kStepThreads)
-    k_collide_stream_x2(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ tags, Grid g,
-                        KParams<float> p, float *__restrict__ partials)
+__device__ __forceinline__ void collide_stream_x2_body(const S *__restrict__ A, S *__restrict__ B,
+                                                       const uint8_t *__restrict__ tags, const Grid &g,
+                                                       const KParams<float> &p, float *__restrict__ partials)
 {
     const int pair = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -952,6 +1064,14 @@ __global__ void __launch_bounds__(kStepThreads)
     // those warps keeps every shuffle of the node work warp-complete
     if (y < g.ny) collide_stream_pair<Q, S, GENERAL, CLOSURE, REDUCE>(A, B, tags, g, p, pair, y, z, ns);
     if constexpr (REDUCE) block_partial_f32(ns, partials + linear_block() * kRedSlots);
+}
+
+template <int Q, typename S, bool GENERAL, int CLOSURE, bool REDUCE>
+__global__ void __launch_bounds__(kStepThreads)
+    k_collide_stream_x2(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ tags, Grid g,
+                        KParams<float> p, float *__restrict__ partials)
+{
+    collide_stream_x2_body<Q, S, GENERAL, CLOSURE, REDUCE>(A, B, tags, g, p, partials);
 }
 
 // ---------------------------------------------------------------------------
@@ -1153,7 +1273,7 @@ __global__ void __launch_bounds__(kStepThreads)
     const T usq15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const T cu = T(cvel(i, 0)) * ux + T(cvel(i, 1)) * uy + T(cvel(i, 2)) * uz;
+        const T cu = cdot<T>(i, ux, uy, uz);
         const T heq = wgt<T>(Q, i) * (dr + r * (cu * (T(3) + T(4.5) * cu) - usq15));
         S v;
         Store<S>::st(&v, heq);
@@ -1235,28 +1355,26 @@ inline void pair_launch_shape(const Grid &g, dim3 &grid, dim3 &block)
     grid = dim3((pairs + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
 }
 
+template <int Q, typename S, bool GEN, bool RED, int CLOSURE>
+void launch_x2(const Launch &L, const KParams<float> &kp, float *partials, dim3 grid, dim3 block)
+{
+    const S *A = (const S *)L.A;
+    S *B = (S *)L.B;
+    k_collide_stream_x2<Q, S, GEN, CLOSURE, RED><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, partials);
+}
+
 template <int Q, typename S, bool GEN, bool RED>
 cudaError_t step_closure_x2(const Launch &L, const KParams<float> &kp, float *partials)
 {
     dim3 grid, block;
     pair_launch_shape(L.g, grid, block);
-    const S *A = (const S *)L.A;
-    S *B = (S *)L.B;
     switch (L.closure) {
-    case LBM_CLOSURE_BGK:
-        k_collide_stream_x2<Q, S, GEN, LBM_CLOSURE_BGK, RED><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, partials);
-        break;
-    case LBM_CLOSURE_SMAGORINSKY:
-        k_collide_stream_x2<Q, S, GEN, LBM_CLOSURE_SMAGORINSKY, RED>
-            <<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, partials);
-        break;
-    case LBM_CLOSURE_TRT:
-        k_collide_stream_x2<Q, S, GEN, LBM_CLOSURE_TRT, RED><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, partials);
-        break;
+    case LBM_CLOSURE_BGK: launch_x2<Q, S, GEN, RED, LBM_CLOSURE_BGK>(L, kp, partials, grid, block); break;
+    case LBM_CLOSURE_SMAGORINSKY: launch_x2<Q, S, GEN, RED, LBM_CLOSURE_SMAGORINSKY>(L, kp, partials, grid, block); break;
+    case LBM_CLOSURE_TRT: launch_x2<Q, S, GEN, RED, LBM_CLOSURE_TRT>(L, kp, partials, grid, block); break;
     case LBM_CLOSURE_STREAM_ONLY:
         if constexpr (RED) return cudaErrorNotSupported;
-        k_collide_stream_x2<Q, S, GEN, LBM_CLOSURE_STREAM_ONLY, false>
-            <<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, nullptr);
+        launch_x2<Q, S, GEN, false, LBM_CLOSURE_STREAM_ONLY>(L, kp, nullptr, grid, block);
         break;
     default: return cudaErrorInvalidValue;
     }
@@ -1283,7 +1401,7 @@ cudaError_t step_closure(const Launch &L, const KParams<typename Store<S>::T> &k
             return cudaGetLastError();
         }
         if constexpr (use_pairs<S>() && PAT == kPatAB) {
-            if (L.g.px >= 64) return step_closure_x2<Q, S, GEN, RED>(L, kp, partials);
+            if (L.g.px >= 64 && !kp.wall_local) return step_closure_x2<Q, S, GEN, RED>(L, kp, partials);
         }
         switch (L.closure) {
         case LBM_CLOSURE_BGK:
@@ -1310,10 +1428,10 @@ cudaError_t step_closure(const Launch &L, const KParams<typename Store<S>::T> &k
 }
 
 // Number of blocks (= partials) a fused step-and-reduce launch writes.
-inline long long fused_partials(const Launch &L, size_t elem)
+inline long long fused_partials(const Launch &L, const lbm_params &p, size_t elem)
 {
     dim3 grid, block;
-    if (elem == 2 && !L.aa && L.g.px >= 64)
+    if (elem == 2 && !L.aa && L.g.px >= 64 && !p.wall_rho_local)
         pair_launch_shape(L.g, grid, block);
     else
         node_launch_shape(L.g, grid, block);
@@ -1338,35 +1456,43 @@ template <int Q, typename S, int PAT> cudaError_t step_reduce_q(const Launch &L,
                      : step_closure<Q, S, false, true, PAT>(L, kp, grid, block, partials);
 }
 
-template <int Q, typename S, int PAT>
-cudaError_t step_compact_q(const Launch &L, const lbm_params &p, const void *Ac, void *Bc, const int *nbr,
-                           long long nfp)
+template <int Q, typename S, int PAT, bool LOCAL>
+cudaError_t step_compact_local(const Launch &L, const KParams<typename Store<S>::T> &kp, const void *Ac, void *Bc,
+                               const int *nbr, long long nfp)
 {
-    const auto kp = make_kparams<typename Store<S>::T>(Q, p);
     const unsigned blocks = (unsigned)((L.n_list + kStepThreads - 1) / kStepThreads);
     if (blocks == 0) return cudaSuccess;
     const S *A = (const S *)Ac;
     S *B = (S *)Bc;
     switch (L.closure) {
     case LBM_CLOSURE_BGK:
-        k_collide_stream_compact<Q, S, LBM_CLOSURE_BGK, PAT>
+        k_collide_stream_compact<Q, S, LBM_CLOSURE_BGK, PAT, LOCAL>
             <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
         break;
     case LBM_CLOSURE_SMAGORINSKY:
-        k_collide_stream_compact<Q, S, LBM_CLOSURE_SMAGORINSKY, PAT>
+        k_collide_stream_compact<Q, S, LBM_CLOSURE_SMAGORINSKY, PAT, LOCAL>
             <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
         break;
     case LBM_CLOSURE_STREAM_ONLY:
-        k_collide_stream_compact<Q, S, LBM_CLOSURE_STREAM_ONLY, PAT>
+        k_collide_stream_compact<Q, S, LBM_CLOSURE_STREAM_ONLY, PAT, LOCAL>
             <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
         break;
     case LBM_CLOSURE_TRT:
-        k_collide_stream_compact<Q, S, LBM_CLOSURE_TRT, PAT>
+        k_collide_stream_compact<Q, S, LBM_CLOSURE_TRT, PAT, LOCAL>
             <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
         break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+template <int Q, typename S, int PAT>
+cudaError_t step_compact_q(const Launch &L, const lbm_params &p, const void *Ac, void *Bc, const int *nbr,
+                           long long nfp)
+{
+    const auto kp = make_kparams<typename Store<S>::T>(Q, p);
+    return kp.wall_local ? step_compact_local<Q, S, PAT, true>(L, kp, Ac, Bc, nbr, nfp)
+                         : step_compact_local<Q, S, PAT, false>(L, kp, Ac, Bc, nbr, nfp);
 }
 
 // Blocks of `threads` threads of `kernel` that fit on the device at once.
