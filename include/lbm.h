@@ -308,9 +308,12 @@ lbm_status lbm_set_closure_weights(lbm_ctx *ctx, const float *params, const floa
  * Errors: ARG, OOM, CUDA. */
 lbm_status lbm_closure_features(lbm_ctx *ctx, float *x, int on_device);
 
-/* dtau[n] for features x[n][7] with the collide kernel's tensor-core tile.
- * All pointers are device memory; asynchronous on stream.  Errors: ARG,
- * CUDA (launch). */
+/* dtau[n] for features x[n][7], batch inference on the 5th-generation
+ * tensor cores (tcgen05: 128 samples per MMA tile, FP32 accumulators in
+ * tensor memory), with the same BF16 roundings as the collide kernel's warp
+ * tile (the FP32 accumulation order may differ).  All pointers are device
+ * memory; asynchronous on stream.  A tile whose completion wait runs out
+ * leaves NaN in its 128 outputs.  Errors: ARG, CUDA (launch). */
 lbm_status lbm_mlp_forward(const float *params, const float *norm, const float *x, int n, float *dtau, void *stream);
 
 /* Bytes of device workspace lbm_mlp_loss_grad needs for n samples. */

@@ -42,19 +42,21 @@ __device__ __forceinline__ float dsilu(float z)
     return s * (1.f + z * (1.f - s));
 }
 
-// Batch inference with the collide kernel's warp tile.
-__global__ void __launch_bounds__(128) k_mlp_forward(const float *__restrict__ P, const float *__restrict__ norm,
-                                                     const float *__restrict__ X, int n, float *__restrict__ dtau)
+// Batch inference with the tcgen05 tile, 128 samples per block.  A tile
+// wait that runs out leaves NaN in that block's outputs.
+__global__ void __launch_bounds__(kTileM) k_mlp_forward(const float *__restrict__ P, const float *__restrict__ norm,
+                                                       const float *__restrict__ X, int n, float *__restrict__ dtau)
 {
-    __shared__ MlpSmem W;
-    __shared__ uint32_t stage[4][32 * 8];
-    load_mlp_smem(P, norm, W, threadIdx.x, blockDim.x);
-    __syncthreads();
+    __shared__ MlpTcNet W;
+    __shared__ MlpTile tile;
+    load_mlp_tc(P, norm, W, threadIdx.x, blockDim.x);
+    mlp_tile_open(tile, threadIdx.x);  // synchronises the block
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     float x[kMlpIn];
 #pragma unroll
-    for (int k = 0; k < kMlpIn; ++k) x[k] = s < n ? X[s * kMlpIn + k] : 0.f;
-    const float d = mlp_warp_dtau(W, stage[threadIdx.x >> 5], x, threadIdx.x & 31u);
+    for (int k = 0; k < kMlpIn; ++k) x[k] = s < n ? X[s * kMlpIn + k] : W.mean[k];
+    const float d = mlp_block_dtau(W, tile, x, threadIdx.x, nullptr);
+    mlp_tile_close(tile, threadIdx.x);
     if (s < n) dtau[s] = d;
 }
 
@@ -334,7 +336,7 @@ lbm_status lbm_mlp_forward(const float *params, const float *norm, const float *
     if (n < 0) return fail(LBM_ERR_ARG, "lbm_mlp_forward: n must be >= 0");
     if (n == 0) return LBM_OK;
     const int blocks = (n + 127) / 128;
-    k_mlp_forward<<<blocks, 128, 0, (cudaStream_t)stream>>>(params, norm, x, n, dtau);
+    k_mlp_forward<<<blocks, kTileM, 0, (cudaStream_t)stream>>>(params, norm, x, n, dtau);
     return launched("lbm_mlp_forward");
 }
 
