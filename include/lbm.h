@@ -368,8 +368,8 @@ lbm_status lbm_info(lbm_ctx *ctx, size_t *population_bytes, int *pitch_x, int *q
  * Computes the same sums as lbm_reduce, without a context, over populations
  * the caller already holds on the device:
  *  h       device array of offset-stripped populations h_i = f_i - w_i in the
- *          storage type of dtype, layout [Q][nz][ny][nx] (x fastest, no
- *          padding, plane stride nx*ny*nz);
+ *          storage type of dtype (LBM_F16_SCALED: h_i * 2^12), layout
+ *          [Q][nz][ny][nx] (x fastest, no padding, plane stride nx*ny*nz);
  *  tags    device array of nx*ny*nz tags (values < LBM_NTAGS), or NULL for
  *          all fluid;
  *  params  only params->force is read (for FORCED nodes); may be NULL;

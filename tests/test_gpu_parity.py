@@ -627,6 +627,49 @@ def test_full_size_tgv512_f32_sampled():
     lat.close()
 
 
+@pytest.mark.parametrize("pattern", ["aa"])
+def test_full_size_tgv512_aa_f32_sampled(pattern):
+    """The in-place pattern at the bench size: after one (odd) step the state
+    is read back from the neighbour-shifted layout, after two from the local
+    one; both sampled against the oracle."""
+    n = 512
+    rho, u = inp.tgv3d(n, 0.04)
+    tau = 0.5 + 3 * 0.04 * (n / (2 * math.pi)) / 1600.0
+    nz = ny = nx = n
+    lat = lbm.Lattice(nx, ny, nz, 19, "f32", pattern=pattern)
+    lat.set_params(tau)
+    lat.init_equilibrium(rho, u)
+    lat.step(1)
+    rng = np.random.default_rng(3)
+    cells = np.stack([rng.integers(0, n, 40), rng.integers(0, n, 40), rng.integers(0, n, 40)], axis=1)
+    cells = np.vstack([cells, [[0, 0, 0], [n - 1, n - 1, n - 1], [0, n - 1, 0], [n - 1, 0, n - 1]]])
+    assert _sampled_check(lat, 19, "f32", rho, u, None, dict(tau=tau), cells) <= 1e-7
+    m1 = lat.reduce()["mass"]
+    lat.step(1)
+    red = lat.reduce()
+    assert abs(red["mass"] - m1) <= 1e-6 * abs(m1) + 1e-3
+    lat.close()
+
+
+@pytest.mark.parametrize("Q,kind", [(27, "f16"), (19, "f16s")])
+def test_full_size_tgv512_half_sampled(Q, kind):
+    """16-bit storage at the precision-study size (512^3; D3Q27 FP16 is that
+    study's configuration): one step from a storage-rounded equilibrium,
+    sampled nodes within half a storage ulp of |h| <~ 0.1 (plus the FP32
+    arithmetic) of the oracle's FP64 step."""
+    n = 512
+    rho, u = inp.tgv3d(n, 0.04)
+    tau = 0.5 + 3 * 0.04 * (n / (2 * math.pi)) / 1600.0
+    lat = make((n, n, n), Q, kind, tau=tau)
+    lat.init_equilibrium(rho, u)
+    lat.step(1)
+    rng = np.random.default_rng(4)
+    cells = np.stack([rng.integers(0, n, 24), rng.integers(0, n, 24), rng.integers(0, n, 24)], axis=1)
+    d = _sampled_check(lat, Q, kind, rho, u, None, dict(tau=tau), cells)
+    assert d <= 1e-4
+    lat.close()
+
+
 def test_full_size_cavity256_f32_sampled():
     n = 256
     tags = inp.cavity_tags(n)

@@ -21,7 +21,9 @@ from paper_2506_09242_gb300 import lbm
 
 pytestmark = pytest.mark.gpu
 
-TORCH_DT = {"f64": torch.float64, "f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
+TORCH_DT = {"f64": torch.float64, "f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16,
+            "f16s": torch.float16}
+SCALE = {"f16s": 4096.0}  # scaled FP16 stores h * 2^12
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -37,7 +39,7 @@ def _close(a, b, rel):
     return abs(a - b) <= rel * max(abs(a), abs(b), 1e-300)
 
 
-@pytest.mark.parametrize("Q,kind", [(19, "f64"), (19, "f32"), (27, "f32"), (19, "f16"), (27, "bf16")])
+@pytest.mark.parametrize("Q,kind", [(19, "f64"), (19, "f32"), (27, "f32"), (19, "f16"), (27, "bf16"), (19, "f16s")])
 def test_noalloc_matches_lbm_reduce(Q, kind):
     shape = (14, 18, 45)
     nz, ny, nx = shape
@@ -54,7 +56,7 @@ def test_noalloc_matches_lbm_reduce(Q, kind):
         lat.get_populations(f)
     _, w, _ = oracle.lattice(Q)
     wd = torch.from_numpy(w).cuda().view(Q, 1, 1, 1)
-    h = (f - wd).to(TORCH_DT[kind]).contiguous()
+    h = ((f - wd) * SCALE.get(kind, 1.0)).to(TORCH_DT[kind]).contiguous()
     tg = torch.from_numpy(tags).cuda()
     rel = 1e-12 if kind == "f64" else 1e-9
     outs = [lbm.reduce_noalloc(h, Q, kind, nx, ny, nz, tags=tg, force=force) for _ in range(2)]
