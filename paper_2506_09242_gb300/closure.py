@@ -62,6 +62,7 @@ class FineRun:
     factor: int
     times: np.ndarray          # convective times of the energy samples
     k_filtered: np.ndarray     # k of the box-filtered velocity
+    k_full: np.ndarray = None  # k of the fine velocity itself (the DNS reference)
     X: object = None           # training features (torch, device)
     y: object = None           # training targets (torch, device)
     y_fields: list = field(default_factory=list)  # (t, full coarse target field) per sample time
@@ -93,7 +94,7 @@ def fine_run(n: int, re: float, factor: int, *, t_end: float = 10.0, k_every: fl
     spt = steps_per_tc(n)
     n_k = int(round(t_end / k_every))
     every = max(1, int(round(sample_every / k_every)))
-    times, ks, Xs, ys, y_fields = [], [], [], [], []
+    times, ks, kf, Xs, ys, y_fields = [], [], [], [], [], []
     done, t_step = 0, 0.0
     diverged = None
     for j in range(n_k + 1):
@@ -112,6 +113,7 @@ def fine_run(n: int, re: float, factor: int, *, t_end: float = 10.0, k_every: fl
         ub = lbm.box_filter(u_d, factor)
         times.append(j * k_every)
         ks.append(0.5 * float((ub * ub).sum(dim=0).mean()))
+        kf.append(0.5 * float((u_d * u_d).sum(dim=0).mean()))
         if j % every == 0 and j > 0:
             X, y = lbm.coarse_samples(rho_d, u_d, factor, tau_c)
             idx = torch.randint(0, X.shape[0], (min(samples_per_snapshot, X.shape[0]),), generator=gen,
@@ -120,7 +122,7 @@ def fine_run(n: int, re: float, factor: int, *, t_end: float = 10.0, k_every: fl
             ys.append(y[idx])
             y_fields.append((j * k_every, y))
     lat.close()
-    run = FineRun(re, n, factor, np.array(times), np.array(ks), diverged_at=diverged)
+    run = FineRun(re, n, factor, np.array(times), np.array(ks), k_full=np.array(kf), diverged_at=diverged)
     run.glups = n ** 3 * done / max(t_step, 1e-9) / 1e9
     run.y_fields = y_fields
     if Xs:
@@ -266,12 +268,13 @@ def calibrate(trained: Trained, n_c: int, fines: dict, train_re, *, alphas=(0.0,
     return best, table
 
 
-def dissipation_error(fine: FineRun, coarse: CoarseRun) -> float:
+def dissipation_error(fine: FineRun, coarse: CoarseRun, reference: str = "filtered") -> float:
     """Relative L2 error of -dk/dt over the fine run's time grid (inf if the
-    coarse run diverged before the end)."""
+    coarse run diverged before the end), against the box-filtered fine run
+    or (reference "fine") the fine run itself."""
     if coarse.diverged_at is not None or len(coarse.times) < len(fine.times):
         return math.inf
-    ef = -np.gradient(fine.k_filtered, fine.times)
+    ef = -np.gradient(fine.k_filtered if reference == "filtered" else fine.k_full, fine.times)
     ec = -np.gradient(coarse.k[:len(fine.times)], coarse.times[:len(fine.times)])
     return float(np.linalg.norm(ec - ef) / np.linalg.norm(ef))
 
@@ -317,6 +320,23 @@ def experiment(n_fine: int, factor: int, train_re, test_re: float, *, t_end: flo
                                    "loss_first_last": [trained2.losses[0][1], trained2.losses[-1][1]],
                                    "feature_std_ce": X.std(dim=0).tolist(), "feature_std_solver": Xa.std(dim=0).tolist()}}
     ref = fines[test_re]
+    # Equal cost: with convective scaling a run of n^3 nodes to a fixed time
+    # costs n^4 / GLUPS, so plain BGK gets the grid n_eq = n_c (GLUPS_bgk /
+    # GLUPS_mlp)^(1/4) (even) for the learned closure's cost; both are judged
+    # against the fine run's own dissipation rate (no box filter fits n_eq).
+    g_mlp = runs["mlp_calibrated"].glups
+    n_eq = 2 * int(round(0.5 * n_c * (runs["bgk"].glups / max(g_mlp, 1e-9)) ** 0.25))
+    eq = coarse_run(n_eq, test_re, "bgk", t_end=t_end)
+    equal_cost = {"n_bgk": n_eq, "glups_bgk": eq.glups, "glups_mlp": g_mlp,
+                  "dissipation_rel_l2_vs_fine": {
+                      f"bgk_{n_eq}": dissipation_error(ref, eq, "fine"),
+                      f"bgk_{n_c}": dissipation_error(ref, runs["bgk"], "fine"),
+                      f"smagorinsky_{n_c}": dissipation_error(ref, runs["smagorinsky"], "fine"),
+                      f"mlp_calibrated_{n_c}": dissipation_error(ref, runs["mlp_calibrated"], "fine")},
+                  "diverged_at_tc": {f"bgk_{n_eq}": eq.diverged_at}}
+    if "mlp_a_posteriori_calibrated" in runs:
+        equal_cost["dissipation_rel_l2_vs_fine"][f"mlp_a_posteriori_calibrated_{n_c}"] = dissipation_error(
+            ref, runs["mlp_a_posteriori_calibrated"], "fine")
     return {
         "n_fine": n_fine, "n_coarse": n_c, "factor": factor, "train_re": list(train_re), "test_re": test_re,
         "t_end_tc": t_end, "train_samples": int(X.shape[0]), "train_steps": steps, "batch": batch,
@@ -327,6 +347,7 @@ def experiment(n_fine: int, factor: int, train_re, test_re: float, *, t_end: flo
         "calibration": {"alpha": alpha, "mean_train_error": {str(a): e for a, e in table.items()}},
         "coarse": {c: {"dissipation_rel_l2": dissipation_error(ref, r), "glups": r.glups,
                        "diverged_at_tc": r.diverged_at} for c, r in runs.items()},
+        "equal_cost": equal_cost,
         **second,
     }
 
