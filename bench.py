@@ -210,7 +210,7 @@ def measured_peak_hbm():
 def time_lattice(lat, steps: int, warmup: int, inner: int, sync_all=None):
     """Times ``steps`` benchmark steps (inner lattice steps + reduction).
 
-    Returns (total_ms, mean collide-stream launch ms, reductions)."""
+    Returns (total_ms, mean collide-stream launch ms, reductions, per-step ms)."""
     import torch
     for _ in range(warmup):
         lat.step(inner - 1)
@@ -235,7 +235,29 @@ def time_lattice(lat, steps: int, warmup: int, inner: int, sync_all=None):
         sync_all()
     total = t0.elapsed_time(t1)
     kernel = sum(a.elapsed_time(b) for a, b in ev) / (steps * (inner - 1))
-    return total, kernel, reds
+    marks = [e[0] for e in ev] + [t1]
+    per_step = [marks[k].elapsed_time(marks[k + 1]) for k in range(steps)]
+    return total, kernel, reds, per_step
+
+
+def d2d_copy_gbs(nbytes: int = 1 << 32, reps: int = 5) -> float:
+    """Bandwidth of a plain device-to-device copy (bytes read + written per
+    second), for context next to the measured peak; torch's copy kernel."""
+    import torch
+    a = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    b.copy_(a)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        b.copy_(a)
+    e1.record()
+    torch.cuda.synchronize()
+    gbs = 2 * nbytes * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del a, b
+    torch.cuda.empty_cache()
+    return gbs
 
 
 def time_e2e(lat, fields, steps: int, inner: int):
@@ -378,7 +400,7 @@ def run_ours(args):
     cells = lat.N
     sampler = ClockSampler(local)
     sampler.start()
-    total_ms, kernel_ms, reds = time_lattice(lat, args.steps, args.warmup, args.inner, sync_all)
+    total_ms, kernel_ms, reds, per_step = time_lattice(lat, args.steps, args.warmup, args.inner, sync_all)
     clocks = sampler.stop()
     glups, total_ms = replica_throughput(total_ms, cells * args.inner * args.steps, dist, "cuda")
 
@@ -398,6 +420,7 @@ def run_ours(args):
     variants = {}
     errors = None
     cpu = None
+    d2d = d2d_copy_gbs() if rank == 0 else None
     if rank == 0 and not args.no_extras:
         for wl, dt, cl, pat in (("tgv512_d3q19", "f16", "bgk", "ab"), ("tgv512_d3q19", "bf16", "bgk", "ab"),
                                 ("cavity256_d3q19", "f32", "bgk", "ab"), ("tgv512_d3q27", "f32", "bgk", "ab"),
@@ -411,7 +434,7 @@ def run_ours(args):
             if (wl, dt, cl, pat) == (args.workload, args.dtype, args.closure, args.pattern):
                 continue
             v, _, d = make_workload(wl, dt, cl, pat)
-            tms, kms, _ = time_lattice(v, 5, 3, args.inner)
+            tms, kms, _, _ = time_lattice(v, 5, 3, args.inner)
             q = int(d["lattice"][3:])
             ach = 2 * q * SIZE[dt] * v.N / (kms * 1e-3) / 1e9
             variants[d["workload"]] = {"glups": v.N * args.inner * 5 / (tms * 1e-3) / 1e9,
@@ -445,6 +468,9 @@ def run_ours(args):
         "e2e": {"value": e2e_glups, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "step": "upload rho,u (FP64, pinned host) + inner lattice steps + reduction read back"},
         "gpu_launches": args.steps * (args.inner + 2),
+        "ms_per_step_spread": {"min": min(per_step), "median": sorted(per_step)[len(per_step) // 2],
+                               "max": max(per_step)},
+        "d2d_copy_gbs": d2d,
         "clocks": clocks,
         "mass_drift": abs(reds[-1]["mass"] - reds[0]["mass"]) / reds[0]["mass"] if reds else None,
         "variants": variants,
