@@ -533,13 +533,14 @@ __device__ __forceinline__ void relax(T (&h)[Q], const Macro<T> &m, T omega, boo
         if (forced) h0 += cf * (w0 * (T(-3) * uG));
         h[0] = h0;
     }
-    if constexpr (Q == 27 || !PAIRED) {
+    if constexpr ((Q == 27 && sizeof(T) == 4) || !PAIRED) {
         // One direction at a time with the full dot products: the same
-        // algebra as the paired form below.  For D3Q27 the 16-bit two-node
-        // kernel compiles this form to 80 registers (the paired form to
-        // 86-90), which keeps six blocks per SM resident instead of five;
-        // the compact kernel (!PAIRED), bound by the latency of its
-        // gathers, is fastest with it as well (measured).
+        // algebra as the paired form below.  For D3Q27 in FP32 the 16-bit
+        // two-node kernel compiles this form to 80 registers (the paired form
+        // to 86-90), which keeps six blocks per SM resident instead of five;
+        // the A/B compact kernel (!PAIRED), bound by the latency of its
+        // gathers, is fastest with it as well (measured).  FP64 compute,
+        // bound by the FP64 rate, takes the paired form.
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
