@@ -7,6 +7,7 @@ second-order equilibrium, the Smagorinsky defining equation, library rounding
 routines, and the performance-model figures printed in Sec. 4.1.
 """
 import itertools
+from pathlib import Path
 
 import numpy as np
 import pytest
@@ -127,12 +128,28 @@ def test_round_storage_keeps_offset():
             assert g[i, n] == w[i] + oracle.round_scalar(f[i, n] - w[i], oracle.BF16)
 
 
+def _golden(name):
+    """key = value fixture of tests/golden (comments after #)."""
+    vals = {}
+    for line in (Path(__file__).parent / "golden" / name).read_text().splitlines():
+        line = line.split("#", 1)[0].strip()
+        if line:
+            k, v = (x.strip() for x in line.split("=", 1))
+            vals[k] = float(v)
+    return vals
+
+
 def test_performance_model_reproduces_paper():
-    """Sec. 4.1: 1.555 TB/s over n_t = 2*19*n_store + 12 bytes gives 9.481 and
-    4.921 GLUPS; the memory-use model (read as n_t L^3 / 40 GB) gives about
-    51% and 99% at L = 500."""
-    assert abs(oracle.glups_peak(1.555e12, 19, 4) - 9.481) < 1e-3
-    assert abs(oracle.glups_peak(1.555e12, 19, 8) - 4.921) < 1e-3
-    for n_store, pct in ((4, 51), (8, 99)):
-        mem = (2 * 19 * n_store + 12) * 500 ** 3 / 40e9
+    """Sec. 4.1: the printed peaks (9.481 and 4.921 GLUPS) and memory-use
+    figures (51% and 99% at L = 500) from the bandwidth over
+    n_t = 2*19*n_store + 12 bytes (fixture tests/golden/performance_model.txt,
+    with the readings of the two garbled formulas)."""
+    g = _golden("performance_model.txt")
+    for n_store, peak in ((g["n_store_sp"], g["peak_glups_sp"]), (g["n_store_dp"], g["peak_glups_dp"])):
+        model = oracle.glups_peak(g["bandwidth_bytes_per_s"], int(g["populations"]), int(n_store),
+                                  int(g["flag_bytes"]))
+        assert abs(model - peak) < 1e-3
+    for n_store, pct in ((g["n_store_sp"], g["memory_percent_sp"]), (g["n_store_dp"], g["memory_percent_dp"])):
+        n_t = 2 * g["populations"] * n_store + g["flag_bytes"]
+        mem = n_t * g["memory_L"] ** 3 / g["gpu_memory_bytes"]
         assert round(100 * mem) == pct
