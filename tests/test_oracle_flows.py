@@ -3,7 +3,8 @@ invariants and brute force.
 
 - streaming direction and bounce-back: a single marker population moves to
   x + c_i (mod n) and reflects off a solid neighbour (exact);
-- mass and momentum invariants to round-off;
+- mass and momentum invariants to round-off, and the momentum Guo's force
+  adds per step (exactly rho g per node, for BGK, TRT and Smagorinsky);
 - the z-extruded 2D Taylor-Green vortex, an exact Navier-Stokes solution:
   amplitude ~ exp(-2 nu k^2 t), with second-order convergence of the rate;
 - plane Poiseuille flow under the Guo body force between halfway bounce-back
@@ -95,6 +96,32 @@ def test_mass_invariant_with_bounce_back_and_force(Q):
     # solid nodes are never updated
     assert np.array_equal(g[:, ~fluid], f[:, ~fluid])
 
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+@pytest.mark.parametrize("closure", [oracle.BGK, oracle.TRT, oracle.SMAGORINSKY])
+def test_guo_force_adds_rho_g_per_step(Q, closure):
+    """With Guo's source every collision adds exactly rho g to a node's
+    momentum: the velocity shift u = (j + rho g / 2) / rho relaxes away
+    omega rho g / 2 and the source's first moment adds (1 - omega / 2) rho g,
+    for each relaxation rate (BGK, both TRT rates, a Smagorinsky tau per
+    node).  On a periodic, fully forced box the total momentum is therefore
+    J0 + n M g after n steps.  Dropping the half-force velocity shift, the
+    (1 - omega/2) factor or a term of the source breaks it."""
+    _, w, _ = oracle.lattice(Q)
+    c, _, _ = oracle.lattice(Q)
+    shape = (6, 7, 8)
+    g_vec = np.array([2e-4, -1e-4, 5e-5])
+    tags = np.full(shape, oracle.FORCED, np.uint8)
+    f = inp.random_populations(w, shape, seed=3, amplitude=0.2)
+    prob = oracle.Problem(Q, 8, 7, 6, tags, tau=0.62, force=tuple(g_vec), closure=closure, cs_smag=0.17)
+    m0 = f.sum()
+    j0 = np.einsum("ia,izyx->a", c, f)
+    n = 25
+    g = prob.step(f, n)
+    assert abs(g.sum() - m0) / m0 <= 1e-12
+    j = np.einsum("ia,izyx->a", c, g)
+    np.testing.assert_allclose(j - j0, n * m0 * g_vec, rtol=1e-10, atol=0)
 
 def _tgv_amplitude(u, n):
     """Projection of u_x on the mode -cos(kx) sin(ky)."""
