@@ -27,7 +27,7 @@ Workflow (no counterpart in the paper; the TGV set-up is Sec. 3.1's):
    learned closure, or the calibrated one. Each is judged by the relative
    L2 error of its dissipation rate -dk/dt against that of the box-filtered
    fine run, where k = <|u|^2 / 2> (Sec. 3.1).
-5. Optionally (a posteriori), a second round trains on inputs taken from
+5. Optionally (a posteriori), a second training stage uses inputs taken from
    the coarse solver's own populations (lbm_closure_features), recorded
    with the calibrated network in the loop and paired with the filtered
    fine targets at the same times.
@@ -285,11 +285,11 @@ def experiment(n_fine: int, factor: int, train_re, test_re: float, *, t_end: flo
     """Fine runs at train_re (and test_re), training, and the three coarse
     runs at test_re; returns a JSON-able summary.
 
-    a_posteriori: a second round trains on the coarse solver's own inputs.
-    The calibrated first-round network runs in the loop of coarse runs at
-    the training Reynolds numbers (solver_samples), the network continues
-    from its first-round weights on those pairs, is recalibrated, and is
-    judged at test_re like the first round."""
+    a_posteriori: a second training stage uses the coarse solver's own
+    inputs.  The calibrated first-stage network runs in the loop of coarse
+    runs at the training Reynolds numbers (solver_samples), the network
+    continues from its first-stage weights on those pairs, is recalibrated,
+    and is judged at test_re like the first stage."""
     import torch
     n_c = n_fine // factor
     fines = {}
@@ -360,7 +360,7 @@ def main(argv=None):  # pragma: no cover - GPU workflow entry point
     ap.add_argument("--t-end", type=float, default=10.0)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--held-out", action="store_true", help="train on Re 800 and 3200, test on 1600")
-    ap.add_argument("--a-posteriori", action="store_true", help="second round on the coarse solver's own inputs")
+    ap.add_argument("--a-posteriori", action="store_true", help="second training stage on the coarse solver's own inputs")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     train_re = (800.0, 3200.0) if a.held_out else (800.0, 1600.0, 3200.0)
