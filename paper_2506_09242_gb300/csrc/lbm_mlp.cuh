@@ -20,7 +20,10 @@
 namespace lbm {
 
 // Shared-memory copy of the network, packed for the mma fragments: BF16
-// pairs (k, k+1) of each output row, inputs padded from 7 to 16.
+// pairs (k, k+1) of each output row, inputs padded from 7 to 16.  Layers 1
+// and 2 hold W/2 and b/2 (exact: a power-of-two scale commutes with BF16 and
+// FP32 rounding), so that their accumulators hold z/2 and
+// SiLU(z) = (z/2)(1 + tanh(z/2)) costs one tanh and one FMA.
 struct __align__(16) MlpSmem {
     uint32_t W1p[kMlpH][8];   // row n: pairs of W1[n][0..15] (cols 7..15 zero)
     uint32_t W2p[kMlpH][16];  // row n: pairs of W2[n][0..31]
@@ -59,17 +62,17 @@ __device__ __forceinline__ void load_mlp_smem(const float *__restrict__ P, const
     const float *b3 = w3 + kMlpH;
     for (int e = tid; e < kMlpH * 8; e += nthreads) {
         const int n = e / 8, k = 2 * (e % 8);
-        const float lo = k < kMlpIn ? W1[n * kMlpIn + k] : 0.f;
-        const float hi = k + 1 < kMlpIn ? W1[n * kMlpIn + k + 1] : 0.f;
+        const float lo = k < kMlpIn ? 0.5f * W1[n * kMlpIn + k] : 0.f;
+        const float hi = k + 1 < kMlpIn ? 0.5f * W1[n * kMlpIn + k + 1] : 0.f;
         sm.W1p[n][e % 8] = pack_bf16(lo, hi);
     }
     for (int e = tid; e < kMlpH * 16; e += nthreads) {
         const int n = e / 16, k = 2 * (e % 16);
-        sm.W2p[n][e % 16] = pack_bf16(W2[n * kMlpH + k], W2[n * kMlpH + k + 1]);
+        sm.W2p[n][e % 16] = pack_bf16(0.5f * W2[n * kMlpH + k], 0.5f * W2[n * kMlpH + k + 1]);
     }
     for (int e = tid; e < kMlpH; e += nthreads) {
-        sm.b1[e] = b1[e];
-        sm.b2[e] = b2[e];
+        sm.b1[e] = 0.5f * b1[e];
+        sm.b2[e] = 0.5f * b2[e];
         sm.w3[e] = w3[e];
     }
     if (tid == 0) {
@@ -111,6 +114,14 @@ __device__ __forceinline__ float silu_f(float z)
     const float hz = 0.5f * z;
     return fmaf(hz, tanh_approx(hz), hz);
 }
+// SiLU of two pre-activations given halved (hz = z/2) as hz + hz tanh(hz);
+// the two FMAs are one FP32x2 FMA, whose lanes round as fmaf does, so the
+// result is bit-identical to silu_f of the full pre-activations.
+__device__ __forceinline__ float2 silu2_half(float hz0, float hz1)
+{
+    const float2 h = make_float2(hz0, hz1);
+    return __ffma2_rn(h, make_float2(tanh_approx(hz0), tanh_approx(hz1)), h);
+}
 __device__ __forceinline__ float softplus_f(float y) { return y > 20.f ? y : log1pf(__expf(y)); }
 
 // The network on 32 nodes at once, one per lane (a warp-collective call:
@@ -120,7 +131,7 @@ __device__ __forceinline__ float softplus_f(float y) { return y > 20.f ? y : log
 // tiles of 8, K = 16 padded inputs), layer 2 is 8 mma per tile (K = 32 in 2
 // steps, the layer-1 results re-packed in registers as the A fragments),
 // layer 3 a dot product reduced over each lane quad.  Accumulators start at
-// the biases.
+// the (halved) biases and end at z/2.
 __device__ __forceinline__ float mlp_warp_dtau(const MlpSmem &W, uint32_t *stage, const float (&x)[kMlpIn],
                                                unsigned lane)
 {
@@ -152,8 +163,9 @@ __device__ __forceinline__ float mlp_warp_dtau(const MlpSmem &W, uint32_t *stage
         for (int t = 0; t < 2; ++t) {
             float c[4] = {bias0, bias1, bias0, bias1};
             mma_bf16(c, a0[t], a1[t], 0u, 0u, b0, b1);
-            a2[t][j >> 1][(j & 1) * 2] = pack_bf16(silu_f(c[0]), silu_f(c[1]));
-            a2[t][j >> 1][(j & 1) * 2 + 1] = pack_bf16(silu_f(c[2]), silu_f(c[3]));
+            const float2 s01 = silu2_half(c[0], c[1]), s23 = silu2_half(c[2], c[3]);
+            a2[t][j >> 1][(j & 1) * 2] = pack_bf16(s01.x, s01.y);
+            a2[t][j >> 1][(j & 1) * 2 + 1] = pack_bf16(s23.x, s23.y);
         }
     }
     // Layer 2 and the output dot product.
@@ -177,8 +189,9 @@ __device__ __forceinline__ float mlp_warp_dtau(const MlpSmem &W, uint32_t *stage
         }
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
-            pg[t] = fmaf(silu_f(c[t][0]), w0, fmaf(silu_f(c[t][1]), w1, pg[t]));
-            pg8[t] = fmaf(silu_f(c[t][2]), w0, fmaf(silu_f(c[t][3]), w1, pg8[t]));
+            const float2 s01 = silu2_half(c[t][0], c[t][1]), s23 = silu2_half(c[t][2], c[t][3]);
+            pg[t] = fmaf(s01.x, w0, fmaf(s01.y, w1, pg[t]));
+            pg8[t] = fmaf(s23.x, w0, fmaf(s23.y, w1, pg8[t]));
         }
     }
 #pragma unroll
