@@ -5,6 +5,8 @@ invariants and brute force.
   x + c_i (mod n) and reflects off a solid neighbour (exact);
 - mass and momentum invariants to round-off, and the momentum Guo's force
   adds per step (exactly rho g per node, for BGK, TRT and Smagorinsky);
+- the reductions against closed-form sums over populations with known
+  moments (forced nodes, skipped walls, a non-finite node);
 - the z-extruded 2D Taylor-Green vortex, an exact Navier-Stokes solution:
   amplitude ~ exp(-2 nu k^2 t), with second-order convergence of the rate;
 - plane Poiseuille flow under the Guo body force between halfway bounce-back
@@ -122,6 +124,47 @@ def test_guo_force_adds_rho_g_per_step(Q, closure):
     assert abs(g.sum() - m0) / m0 <= 1e-12
     j = np.einsum("ia,izyx->a", c, g)
     np.testing.assert_allclose(j - j0, n * m0 * g_vec, rtol=1e-10, atol=0)
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_reduce_closed_form_sums(Q):
+    """The reductions (Sec. 3.1's k = <|u|^2 / 2> over fluid nodes, with the
+    mass, momentum, velocity sum, rho-weighted energy, max |u| and counts
+    beside it) on populations with known moments: f_i = w_i rho (1 + 3 c_i.m)
+    has sum rho and first moment rho m by the lattice's isotropy.  Plain
+    fluid nodes take m = u.  Forced nodes hold post-collision populations,
+    whose first moment is rho (u + g/2) for the velocity u their collision
+    used, so m = u + g/2 must report u.  Solid and wall nodes hold NaN and
+    are skipped; one fluid node holding a NaN is counted as fluid and as
+    non-finite and left out of every sum."""
+    c, w, _ = oracle.lattice(Q)
+    shape = (5, 6, 7)
+    rng = np.random.default_rng(11)
+    tags = rng.choice(np.array([oracle.FLUID, oracle.FORCED, oracle.SOLID, oracle.WALL0 + 1], np.uint8),
+                      size=shape, p=[0.4, 0.4, 0.1, 0.1])
+    fluid = tags <= oracle.FORCED
+    bad = tuple(int(i[0]) for i in np.nonzero(fluid))  # first fluid node: non-finite
+    g_vec = np.array([3e-3, -2e-3, 1e-3])
+    rho = rng.uniform(0.9, 1.1, shape)
+    u = rng.uniform(-0.05, 0.05, (3,) + shape)
+    m = u + np.where(tags == oracle.FORCED, 1.0, 0.0)[None] * (0.5 * g_vec)[:, None, None, None]
+    f = w[:, None, None, None] * rho[None] * (1.0 + 3.0 * np.einsum("ia,azyx->izyx", c, m))
+    f[:, ~fluid] = np.nan
+    f[(3,) + bad] = np.nan
+    prob = oracle.Problem(Q, 7, 6, 5, tags, tau=0.8, force=tuple(g_vec))
+    red = prob.reduce(f)
+
+    ok = fluid.copy()
+    ok[bad] = False
+    usq = np.sum(u * u, axis=0)
+    assert red["n_fluid"] == int(fluid.sum()) and red["nonfinite"] == 1
+    assert red["mass"] == pytest.approx(rho[ok].sum(), rel=1e-13)
+    for a in range(3):
+        assert red["mom"][a] == pytest.approx((rho * u[a])[ok].sum(), rel=1e-11, abs=1e-15)
+        assert red["vel"][a] == pytest.approx(u[a][ok].sum(), rel=1e-11, abs=1e-15)
+    assert red["ke"] == pytest.approx(0.5 * usq[ok].sum(), rel=1e-12)
+    assert red["ke_rho"] == pytest.approx(0.5 * (rho * usq)[ok].sum(), rel=1e-12)
+    assert red["umax"] == pytest.approx(np.sqrt(usq[ok].max()), rel=1e-12)
 
 def _tgv_amplitude(u, n):
     """Projection of u_x on the mode -cos(kx) sin(ky)."""
