@@ -5,6 +5,8 @@ invariants and brute force.
   x + c_i (mod n) and reflects off a solid neighbour (exact);
 - mass and momentum invariants to round-off, and the momentum Guo's force
   adds per step (exactly rho g per node, for BGK, TRT and Smagorinsky);
+- Smagorinsky at Cs = 0 and the learned closure with a zero output scale or
+  a constant output reduce to BGK;
 - the reductions against closed-form sums over populations with known
   moments (forced nodes, skipped walls, a non-finite node);
 - the z-extruded 2D Taylor-Green vortex, an exact Navier-Stokes solution:
@@ -411,6 +413,38 @@ def test_trt_reduces_to_bgk_when_both_rates_match():
     trt = oracle.Problem(Q, 8, 7, 6, tags, closure=oracle.TRT, trt_magic=(tau - 0.5) ** 2, **kw).step(f0, 10)
     assert np.max(np.abs(trt - bgk)) <= 1e-15
 
+
+
+def test_relaxation_time_closures_reduce_to_bgk():
+    """Special cases that reduce to plain BGK: Smagorinsky with Cs = 0, the
+    learned closure with a zero output scale (dtau = 0), and the learned
+    closure whose last layer has zero weights, so that its output is the
+    constant dtau = scale * softplus(b3) at every node: BGK at tau + dtau."""
+    Q = 19
+    _, w, _ = oracle.lattice(Q)
+    shape = (6, 7, 8)
+    tags = inp.random_tags(shape, seed=4, p_solid=0.2, p_forced=0.3, p_wall=0.05, n_walls=1)
+    f0 = inp.random_populations(w, shape, seed=5, amplitude=0.1)
+    tau = 0.71
+    kw = dict(force=(1e-4, 2e-5, 0.0), wall_u=[(0.01, 0.0, 0.0)])
+    bgk = oracle.Problem(Q, 8, 7, 6, tags, tau=tau, **kw).step(f0, 10)
+    smag0 = oracle.Problem(Q, 8, 7, 6, tags, tau=tau, closure=oracle.SMAGORINSKY, cs_smag=0.0, **kw).step(f0, 10)
+    assert np.array_equal(smag0, bgk)
+
+    P = inp.mlp_init(6)
+    norm = np.concatenate([np.zeros(7), np.ones(7), [0.0, 0.0]])
+    mlp0 = oracle.Problem(Q, 8, 7, 6, tags, tau=tau, closure=oracle.MLP, mlp_params=P, mlp_norm=norm, **kw)
+    assert np.array_equal(mlp0.step(f0, 10), bgk)
+
+    P = P.copy()
+    P[-33:-1] = 0.0  # w3 = 0
+    P[-1] = 0.4      # b3
+    norm[14] = 0.05  # output scale
+    dtau = oracle.mlp_dtau(P, norm, np.ones(7))
+    assert dtau == pytest.approx(0.05 * math.log1p(math.exp(0.4)), rel=1e-15)
+    const = oracle.Problem(Q, 8, 7, 6, tags, tau=tau, closure=oracle.MLP, mlp_params=P, mlp_norm=norm, **kw)
+    shifted = oracle.Problem(Q, 8, 7, 6, tags, tau=tau + dtau, **kw)
+    assert np.max(np.abs(const.step(f0, 10) - shifted.step(f0, 10))) <= 1e-15
 
 @pytest.mark.parametrize("tau", [0.6, 1.0, 1.7])
 def test_trt_magic_poiseuille_is_exact_at_any_tau(tau):
