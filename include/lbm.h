@@ -254,6 +254,33 @@ lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int on_device);
  * Does not reset the step counter.  Asynchronous for device inputs. */
 lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device);
 
+/* Bit-exact checkpoints (Sec. 2.3.2 mentions checkpointing of serialized
+ * data but gives no mechanism).  The FP64 round trip of
+ * lbm_get_populations / lbm_set_populations adds and removes the offset w_i,
+ * which can round away the smallest stored deviations; these two calls move
+ * the stored state itself.
+ *
+ * lbm_get_state copies the population array byte for byte: the
+ * offset-stripped values h_i in the storage type, in the library's padded
+ * layout (Q planes of population_bytes / Q bytes each; rows of pitch_x nodes;
+ * both from lbm_info).  *layout receives 0 for the local layout, or 1 for the
+ * AA pattern's neighbour-shifted layout after an odd number of steps;
+ * *steps the step counter (either pointer may be NULL).  bytes must equal
+ * lbm_info's population_bytes.  buf is host memory (on_device = 0, pageable
+ * is fine) or device memory (1).  Synchronizes.  Errors: ARG (NULL context
+ * or buffer, wrong size), CUDA. */
+lbm_status lbm_get_state(lbm_ctx *ctx, void *buf, size_t bytes, int *layout, long long *steps, int on_device);
+
+/* Restores a state written by lbm_get_state into a context of the same
+ * size, lattice, storage type and pattern (into both arrays with
+ * LBM_PATTERN_AB), with its layout word and step counter.  Tags, parameters
+ * and closure weights are not part of the state: set them first
+ * (lbm_set_tags is refused once layout 1 is restored).  Stepping on then
+ * gives, on every fluid node, the same bits as the run that was saved.
+ * Synchronizes.  Errors: ARG (NULL context or buffer, wrong size, layout not
+ * 0 or 1, layout 1 without the AA pattern, steps < 0), CUDA. */
+lbm_status lbm_set_state(lbm_ctx *ctx, const void *buf, size_t bytes, int layout, long long steps, int on_device);
+
 /* Random overlapping spheres as a porous medium: the synthetic stand-in for
  * the Berea sandstone volume of Sec. 3.3.  centres[n][3] (host, integer node
  * coordinates, any value: wrapped periodically) and radii[n] (host, in

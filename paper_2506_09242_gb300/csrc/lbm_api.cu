@@ -958,6 +958,43 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device)
     return on_device ? LBM_OK : sync(ctx);
 }
 
+lbm_status lbm_get_state(lbm_ctx *ctx, void *buf, size_t bytes, int *layout, long long *steps, int on_device)
+{
+    if (!ctx || !buf) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    if (bytes != ctx->pop_bytes)
+        return fail(ctx, LBM_ERR_ARG, "state buffer of %zu bytes, the state has %zu", bytes, ctx->pop_bytes);
+    ENSURE_DENSE(ctx);
+    CUDA_TRY(ctx,
+             cudaMemcpyAsync(buf, ctx->A, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             ctx->stream),
+             "state copy");
+    lbm_status s = sync(ctx);
+    if (s != LBM_OK) return s;
+    if (layout) *layout = (ctx->aa && ctx->aa_p) ? 1 : 0;
+    if (steps) *steps = ctx->steps;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_ctx *ctx, const void *buf, size_t bytes, int layout, long long steps, int on_device)
+{
+    if (!ctx || !buf) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    if (bytes != ctx->pop_bytes)
+        return fail(ctx, LBM_ERR_ARG, "state buffer of %zu bytes, the state has %zu", bytes, ctx->pop_bytes);
+    if (layout != 0 && layout != 1) return fail(ctx, LBM_ERR_ARG, "layout must be 0 or 1");
+    if (layout == 1 && !ctx->aa) return fail(ctx, LBM_ERR_ARG, "layout 1 exists only with the AA pattern");
+    if (steps < 0) return fail(ctx, LBM_ERR_ARG, "steps must be >= 0");
+    CUDA_TRY(ctx,
+             cudaMemcpyAsync(ctx->A, buf, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             ctx->stream),
+             "state copy");
+    if (!ctx->aa)
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->B, ctx->A, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "state copy");
+    dense_written(ctx);
+    ctx->aa_p = layout == 1;
+    ctx->steps = steps;
+    return sync(ctx);
+}
+
 lbm_status lbm_geometry_spheres(lbm_ctx *ctx, const int32_t *centres, const double *radii, int n_spheres,
                                 double target_porosity, uint8_t pore_tag, int *n_used, double *porosity)
 {

@@ -102,6 +102,8 @@ SIGNATURES = {
     "lbm_sync": (_I, [_P, _I]),
     "lbm_get_populations": (_I, [_P, _P, _I]),
     "lbm_set_populations": (_I, [_P, _P, _I]),
+    "lbm_get_state": (_I, [_P, _P, _SZ, ctypes.POINTER(_I), ctypes.POINTER(_LL), _I]),
+    "lbm_set_state": (_I, [_P, _P, _SZ, _I, _LL, _I]),
     "lbm_info": (_I, [_P, ctypes.POINTER(_SZ), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "lbm_last_error": (ctypes.c_char_p, [_P]),
     "lbm_geometry_spheres": (_I, [_P, _P, _P, _I, _D, ctypes.c_uint8, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
@@ -225,6 +227,7 @@ class Lattice:
         _check(lib.lbm_create_ex(nx, ny, nz, self.Q, self.dtype, self.pattern, alloc_ptr, stream_handle,
                                  ctypes.byref(ctx)))
         self._ctx = ctx
+        self._closure = None  # host copy of the closure weights, for checkpoints
         self.params = Params()
         self.params.tau = 1.0
         self.params.rho_wall = 1.0
@@ -363,6 +366,57 @@ class Lattice:
         self._call("lbm_set_populations", p, d)
         self._keep = keep
 
+    def get_state(self):
+        """(raw, layout, steps): the stored populations byte for byte (storage
+        type, padded layout), the layout word (1 after an odd number of AA
+        steps, else 0) and the step counter; for bit-exact checkpoints."""
+        raw = np.empty(self.info()["population_bytes"], dtype=np.uint8)
+        layout, steps = ctypes.c_int(), ctypes.c_longlong()
+        self._call("lbm_get_state", raw.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(raw.nbytes),
+                   ctypes.byref(layout), ctypes.byref(steps), 0)
+        return raw, layout.value, steps.value
+
+    def set_state(self, raw, layout: int = 0, steps: int = 0):
+        """Restores what get_state returned (set tags, parameters and closure
+        weights first)."""
+        raw = np.ascontiguousarray(raw, dtype=np.uint8).reshape(-1)
+        self._call("lbm_set_state", raw.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(raw.nbytes), int(layout),
+                   int(steps), 0)
+
+    def save_checkpoint(self, path):
+        """Writes everything a run needs to continue bit for bit to an .npz
+        file: the raw state, layout word and step counter, the tags, the
+        parameters, the closure weights if set, and the lattice's shape,
+        velocity set, storage type and streaming pattern."""
+        raw, layout, steps = self.get_state()
+        extra = {}
+        if self._closure is not None:
+            extra = {"closure_params": self._closure[0], "closure_norm": self._closure[1]}
+        np.savez(path, state=raw, layout=layout, steps=steps, tags=self.get_tags(),
+                 params=np.frombuffer(bytes(self.params), dtype=np.uint8),
+                 meta=np.array([self.nx, self.ny, self.nz, self.Q, self.dtype, self.pattern], dtype=np.int64),
+                 **extra)
+
+    @classmethod
+    def from_checkpoint(cls, path, **kwargs):
+        """A new lattice holding the state save_checkpoint wrote (kwargs go to
+        the constructor: device, stream, torch_allocator)."""
+        with np.load(path) as d:
+            nx, ny, nz, Q, dtype, pattern = (int(v) for v in d["meta"])
+            lat = cls(nx, ny, nz, Q, dtype, pattern=pattern, **kwargs)
+            try:
+                lat.set_tags(d["tags"])
+                p = Params.from_buffer_copy(d["params"].tobytes())
+                lat._call("lbm_set_params", ctypes.byref(p))
+                lat.params = p
+                if "closure_params" in d:
+                    lat.set_closure_weights(d["closure_params"], d["closure_norm"])
+                lat.set_state(d["state"], int(d["layout"]), int(d["steps"]))
+            except Exception:
+                lat.close()
+                raise
+        return lat
+
     def geometry_spheres(self, centres, radii, target_porosity: float, pore_tag: int = TAG_FLUID):
         """Random-sphere medium; returns (n_used, porosity)."""
         c = np.ascontiguousarray(centres, dtype=np.int32)
@@ -381,11 +435,13 @@ class Lattice:
 
     def set_closure_weights(self, params, norm):
         """Installs the closure network (params[1345], norm[16]; numpy or CUDA tensors)."""
-        p, dp, _kp = _buf(params, np.float32)
-        n, dn, _kn = _buf(norm, np.float32)
+        p, dp, kp = _buf(params, np.float32)
+        n, dn, kn = _buf(norm, np.float32)
         if dp != dn:
             raise ValueError("params and norm must both be on the host or both on the device")
         self._call("lbm_set_closure_weights", p, n, dp)
+        host = [k.detach().cpu().numpy() if hasattr(k, "detach") else k for k in (kp, kn)]
+        self._closure = (np.array(host[0], dtype=np.float32), np.array(host[1], dtype=np.float32))
 
     def closure_features(self, out=None):
         """The closure's inputs for the next step, (N, 7) FP32 with N in

@@ -79,6 +79,9 @@ def test_allocator_failure_is_reported_as_oom(lib):
 
 def test_null_context_calls_fail_cleanly(lib):
     assert lib.lbm_step(None, 1) == lbm.ERR_ARG
+    buf = ctypes.create_string_buffer(64)
+    assert lib.lbm_get_state(None, buf, 64, None, None, 0) == lbm.ERR_ARG
+    assert lib.lbm_set_state(None, buf, 64, 0, 0, 0) == lbm.ERR_ARG
     assert lib.lbm_destroy(None) == lbm.OK
     assert lib.lbm_sync(None, 0) == lbm.ERR_ARG
 
