@@ -136,13 +136,16 @@ class ClockSampler:
     def start(self):
         try:
             import tempfile
-            self.path = tempfile.mktemp(suffix=".csv")
-            self.out = open(self.path, "w")
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            self.out = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
                  "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
-        except (OSError, FileNotFoundError):
+        except OSError:  # no nvidia-smi: no clock record
             self.proc = None
+            if self.path:
+                self.out.close()
+                os.unlink(self.path)
 
     def stop(self):
         if self.proc is None:
@@ -153,24 +156,33 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.out.close()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm = float(parts[1].split()[0])
-                smax = float(parts[2].split()[0])
-            except ValueError:
-                continue
-            rows.append((sm, smax, parts[5:9]))
+        with open(self.path) as fh:
+            summary = parse_clock_samples(fh)
         os.unlink(self.path)
-        if not rows:
-            return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for _, _, flags in rows for k, f in enumerate(flags) if f.lower() == "active"})
-        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+        return summary
+
+
+def parse_clock_samples(lines):
+    """Summary of nvidia-smi rows in ClockSampler.FIELDS order: the median SM
+    clock, the largest maximum clock, and the slowdown reasons seen Active in
+    any row; None when no row parses."""
+    rows = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm = float(parts[1].split()[0])
+            smax = float(parts[2].split()[0])
+        except (ValueError, IndexError):
+            continue
+        rows.append((sm, smax, parts[5:9]))
+    if not rows:
+        return None
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[k] for _, _, flags in rows for k, f in enumerate(flags) if f.lower() == "active"})
+    return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+            "reasons": reasons, "samples": len(rows)}
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,40 @@
+"""Host logic of bench.py that needs no GPU: the clock-record summary and
+the gate that reports recorded ncu traffic only for the kernel source it was
+measured on."""
+import sys
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parents[1]
+sys.path.insert(0, str(ROOT))
+import bench  # noqa: E402
+
+
+def test_clock_summary_median_max_and_reasons():
+    rows = [
+        "0, 2070 MHz, 2070 MHz, 900.10 W, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055 MHz, 2070 MHz, 1390.00 W, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2040 MHz, 2070 MHz, 1398.50 W, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+        "0, [N/A], 2070 MHz, 1.0 W, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    s = bench.parse_clock_samples(rows)
+    assert s == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = rows[:1] + ["0, 1500 MHz, 2070 MHz, 1.0 W, 0x8, Active, Not Active, Active, Not Active"]
+    assert bench.parse_clock_samples(hot)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert bench.parse_clock_samples(["nothing here"]) is None
+
+
+def test_recorded_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_2506_09242_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "lbm_kernels.cuh").write_text("// kernel v1\n")
+    (csrc / "lbm_internal.cuh").write_text("// internals\n")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", tmp_path)
+    h = bench.kernel_source_hash()
+    (tmp_path / "profiles" / "k.md").write_text(
+        f"workload: tgv3d_64_d3q19_f32\ntraffic_bytes_per_launch: 1.5e9\nkernel_source_sha256_16: {h}\n")
+    assert bench.recorded_traffic("tgv3d_64_d3q19_f32") == 1.5e9
+    assert bench.recorded_traffic("tgv3d_128_d3q19_f32") is None
+    (csrc / "lbm_kernels.cuh").write_text("// kernel v2\n")
+    assert bench.recorded_traffic("tgv3d_64_d3q19_f32") is None
