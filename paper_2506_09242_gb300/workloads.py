@@ -8,6 +8,8 @@
 - ``tgv_precision``: the 3D Taylor-Green vortex of Sec. 3.1 with FP64, FP32,
   FP16- and BF16-shifted storage. Records kinetic energy and enstrophy curves
   and the velocity error against the FP64 run at chosen times.
+- ``size_sweep``: GLUPS against the lattice's share of device memory (the
+  performance-versus-domain-size study of Sec. 4.1).
 
 torch is used for device buffers, for differences of fields when evaluating
 errors and for time averages of velocity fields.
@@ -229,6 +231,60 @@ def cavity_study(sizes=(128, 256), *, re: float = 1000.0, t_max: float = 80.0, r
     return out
 
 
+STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "f16s": 2}
+
+
+def sweep_plan(sizes, Q: int, dtype: str, pattern: str, device_bytes: int, free_bytes: int, *,
+               headroom: float = 0.8):
+    """The cubes of the size sweep that fit: (n, population bytes, fraction of
+    the device memory) for every n whose population arrays (two with the A/B
+    pattern, one with AA; rows padded to 32 nodes) take at most headroom of
+    the free memory.  The memory fraction is the x-axis of the paper's
+    performance-versus-memory-use figure (Sec. 4.1)."""
+    arrays = 1 if pattern == "aa" else 2
+    plan = []
+    for n in sizes:
+        px = (n + 31) // 32 * 32
+        plane = (px * n * n + 255) // 256 * 256
+        nbytes = arrays * Q * plane * STORAGE_BYTES[dtype]
+        if nbytes <= headroom * free_bytes:
+            plan.append((n, nbytes, nbytes / device_bytes))
+    return plan
+
+
+def size_sweep(sizes=(64, 96, 128, 192, 256, 320, 384, 512, 640, 768, 896, 1024), *, Q: int = 19,
+               dtype: str = "f32", pattern: str = "ab", steps: int = 40, peak_gbs: float | None = None) -> dict:
+    """GLUPS of the periodic BGK step against the lattice's share of device
+    memory, the analogue of the paper's study of performance versus domain
+    size (Sec. 4.1, which finds performance rising with memory use).  Each
+    size is timed with CUDA events over `steps` steps after 4 warm-up steps;
+    sizes whose arrays would not fit in 80% of the free memory are skipped."""
+    import torch
+    free, total = torch.cuda.mem_get_info()
+    rows = []
+    for n, nbytes, frac_mem in sweep_plan(sizes, Q, dtype, pattern, total, free):
+        with lbm.Lattice(n, n, n, Q, dtype, pattern=pattern) as lat:
+            lat.set_params(0.6)
+            lat.init_equilibrium()
+            lat.step(4)
+            _sync()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record()
+            lat.step(steps)
+            t1.record()
+            _sync()
+            ms = t0.elapsed_time(t1) / steps
+        torch.cuda.empty_cache()
+        glups = n ** 3 / (ms * 1e-3) / 1e9
+        gbs = 2 * Q * STORAGE_BYTES[dtype] * n ** 3 / (ms * 1e-3) / 1e9
+        row = {"n": n, "memory_fraction": frac_mem, "population_gb": nbytes / 1e9, "ms_per_step": ms,
+               "glups": glups, "gbs": gbs}
+        if peak_gbs:
+            row["frac_of_peak"] = gbs / peak_gbs
+        rows.append(row)
+    return {"Q": Q, "dtype": dtype, "pattern": pattern, "steps": steps, "device_bytes": total, "rows": rows}
+
+
 def tgv_precision(n: int = 512, Q: int = 27, *, dtypes=("f64", "f32", "f16", "bf16", "f16s"), u0: float = 0.04,
                   re: float = 1600.0, t_end: float = 10.0, every: float = 0.5, error_at=(1.0, 5.0, 10.0)) -> dict:
     """Runs the TGV once per storage type (FP64 first) and compares each
@@ -280,9 +336,13 @@ def tgv_precision(n: int = 512, Q: int = 27, *, dtypes=("f64", "f32", "f16", "bf
 def main(argv=None):  # pragma: no cover - GPU workflow entry point
     import argparse
     ap = argparse.ArgumentParser(description="reference workloads")
-    ap.add_argument("which", choices=["porous", "porous_tau", "cavity", "cavity_study", "tgv_precision"])
+    ap.add_argument("which", choices=["porous", "porous_tau", "cavity", "cavity_study", "tgv_precision",
+                                      "size_sweep"])
+    ap.add_argument("--dtype", default="f32", choices=sorted(STORAGE_BYTES))
+    ap.add_argument("--pattern", default="ab", choices=("ab", "aa"))
     ap.add_argument("--n", type=int, default=None)
-    ap.add_argument("--Q", type=int, default=27)
+    ap.add_argument("--Q", type=int, default=None, choices=(19, 27),
+                    help="velocity set (tgv_precision: 27, size_sweep: 19 when not given)")
     ap.add_argument("--t-end", type=float, default=10.0)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
@@ -294,8 +354,10 @@ def main(argv=None):  # pragma: no cover - GPU workflow entry point
         res = cavity(a.n or 256)
     elif a.which == "cavity_study":
         res = cavity_study()
+    elif a.which == "size_sweep":
+        res = size_sweep(Q=a.Q or 19, dtype=a.dtype, pattern=a.pattern)
     else:
-        res = tgv_precision(a.n or 512, a.Q, t_end=a.t_end)
+        res = tgv_precision(a.n or 512, a.Q or 27, t_end=a.t_end)
     text = json.dumps(res, indent=1)
     print(text)
     if a.out:

@@ -23,3 +23,24 @@ def test_cavity_profiles_pick_the_centrelines(n):
     assert np.allclose(uz, (np.cos(k) - 3.0) / 0.5, rtol=0, atol=1e-15)
     assert xi[0] == pytest.approx(0.5 / (n - 2)) and xi[0] + xi[-1] == pytest.approx(1.0)
     assert np.all(np.diff(xi) > 0)
+
+
+def test_size_sweep_plan_counts_the_population_arrays():
+    """Two arrays with A/B, one with AA; rows padded to 32 nodes and planes
+    to 256 values; sizes past 80% of the free memory are left out."""
+    gb = 10 ** 9
+    plan = workloads.sweep_plan([64, 100, 512, 1024], 19, "f32", "ab", device_bytes=284 * gb, free_bytes=280 * gb)
+    sizes = [n for n, _, _ in plan]
+    assert sizes == [64, 100, 512, 1024]
+    by_n = {n: b for n, b, _ in plan}
+    assert by_n[512] == 2 * 19 * 512 ** 3 * 4          # 20.4 GB, as the bench reports
+    px = 128                                             # 100 padded to a multiple of 32
+    plane = (px * 100 * 100 + 255) // 256 * 256
+    assert by_n[100] == 2 * 19 * plane * 4
+    assert by_n[1024] == 2 * 19 * 1024 ** 3 * 4          # 163 GB: fits in 80% of 280 GB
+    tight = workloads.sweep_plan([512, 1024], 19, "f32", "ab", device_bytes=284 * gb, free_bytes=150 * gb)
+    assert [n for n, _, _ in tight] == [512]
+    aa = workloads.sweep_plan([1024], 19, "f64", "aa", device_bytes=284 * gb, free_bytes=280 * gb)
+    assert aa[0][1] == 19 * 1024 ** 3 * 8 and aa[0][2] == pytest.approx(19 * 8 * 1024 ** 3 / (284 * gb))
+    # D3Q27 FP64 at 1024^3 needs 232 GB even with AA: more than 80% of 280 GB
+    assert workloads.sweep_plan([1024], 27, "f64", "aa", device_bytes=284 * gb, free_bytes=280 * gb) == []
