@@ -43,10 +43,13 @@
  *
  * Parity pins: tests/test_oracle_*.py check this file against closed forms
  * (lattice isotropy, equilibrium moments, plane Poiseuille and Couette flow,
- * the decay of a 2D Taylor-Green vortex, exact polynomial differentiation),
- * conservation invariants and brute force.  The MLP closure step inside
- * orc_step is pinned against the numpy FP64 MLP in oracle/mlp.py, which is
- * itself pinned by finite differences.
+ * the decay of a 2D Taylor-Green vortex, exact polynomial differentiation,
+ * the momentum rho g that Guo's source adds per step, reductions of
+ * populations with known moments), conservation invariants, special cases
+ * that reduce to BGK (TRT with equal rates, Smagorinsky at Cs = 0, a closure
+ * with zero or constant output) and brute force.  The MLP closure step
+ * inside orc_step is pinned against the numpy FP64 MLP in oracle/mlp.py,
+ * which is itself pinned by finite differences.
  */
 #include <math.h>
 #include <stddef.h>
