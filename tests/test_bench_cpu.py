@@ -38,3 +38,34 @@ def test_recorded_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
     assert bench.recorded_traffic("tgv3d_128_d3q19_f32") is None
     (csrc / "lbm_kernels.cuh").write_text("// kernel v2\n")
     assert bench.recorded_traffic("tgv3d_64_d3q19_f32") is None
+
+
+def test_clock_sampler_runs_a_sampling_process(tmp_path, monkeypatch):
+    """start/stop around a stand-in nvidia-smi that prints two rows and
+    waits: the rows are parsed and the temporary record is removed."""
+    import os
+    import time
+
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '0, 2070 MHz, 2070 MHz, 800.00 W, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo '0, 2040 MHz, 2070 MHz, 1390.00 W, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                    "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ['PATH']}")
+    s = bench.ClockSampler(0)
+    s.start()
+    assert s.proc is not None
+    time.sleep(0.5)
+    summary = s.stop()
+    assert summary == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 2}
+    assert not os.path.exists(s.path)
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    import os
+    monkeypatch.setenv("PATH", str(tmp_path))  # an empty directory: no nvidia-smi
+    s = bench.ClockSampler(0)
+    s.start()
+    assert s.proc is None and not os.path.exists(s.path)
+    assert s.stop() is None
