@@ -41,3 +41,17 @@ def test_oracle_imports_nothing_of_the_package():
 
 def test_input_generators_are_independent_of_both():
     assert not {"oracle", "paper_2506_09242_gb300"} & _imports(ROOT / "lbm_inputs.py")
+
+
+def test_bench_uses_the_oracle_only_in_its_baseline_legs():
+    """bench.py may run the oracle only for the CPU baseline and the
+    reference arm; the timed GPU path never imports it."""
+    tree = ast.parse((ROOT / "bench.py").read_text())
+    users = set()
+    for fn in [n for n in ast.walk(tree) if isinstance(n, ast.FunctionDef)]:
+        for node in ast.walk(fn):
+            if isinstance(node, ast.Import) and any(a.name == "oracle" for a in node.names):
+                users.add(fn.name)
+    top = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))]
+    assert not any(isinstance(n, ast.Import) and any(a.name == "oracle" for a in n.names) for n in top)
+    assert users == {"oracle_glups", "run_reference"}
