@@ -383,8 +383,11 @@ lbm_status lbm_box_filter(const double *in, int ncomp, int nx, int ny, int nz, i
  * number of populations.  Any pointer may be NULL. */
 lbm_status lbm_info(lbm_ctx *ctx, size_t *population_bytes, int *pitch_x, int *q);
 
-/* Largest lattice lbm_reduce_noalloc accepts (32-bit node offsets). */
-#define LBM_NOALLOC_MAX_NODES 2147483647LL
+/* Largest lattice lbm_reduce_noalloc accepts: 2^31 - 257 nodes, the bound
+ * lbm_create puts on padded lattices.  The reduction walks node offsets in
+ * 32-bit integers, each thread stepping by its block's 256 threads, so the
+ * last offset a thread forms is below N + 256 and stays representable. */
+#define LBM_NOALLOC_MAX_NODES 2147483391LL
 
 /* Domain reduction that allocates no memory (the paper has no counterpart;
  * it exists for callers that cannot allocate device memory: a host code that
@@ -403,10 +406,12 @@ lbm_status lbm_info(lbm_ctx *ctx, size_t *population_bytes, int *pitch_x, int *q
  *  stream  cudaStream_t to run on (NULL: legacy default stream);
  *  out     host struct, filled on LBM_OK and on LBM_ERR_UNSTABLE.
  * Scratch: the per-block partials live in a file-scope device array of
- * 117,888 bytes that every GPU loading the library holds until exit; calls
- * never call cudaMalloc, cudaFree or any allocating routine.  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress), so
- * that first call should come before any stream capture.  All calls share the
+ * 116,832 bytes (1,217 x 12 doubles) that every GPU loading the library holds
+ * until exit; calls never call cudaMalloc, cudaFree or any allocating
+ * routine.  The first successful call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and keeps it; a failed lookup is not kept,
+ * so a later call retries it.  That first call should come before any stream
+ * capture.  All calls share the
  * array: calls that overlap on the GPU race and must be serialised by the
  * caller.  Synchronizes the stream.  Errors: ARG (NULL pointer, bad enum,
  * a size < 1, more than LBM_NOALLOC_MAX_NODES nodes), CUDA, UNSTABLE. */

@@ -11,15 +11,15 @@
 // instead of in allocated memory.
 //
 // The array is a static device variable: every GPU that loads this library
-// holds it (117,888 bytes) until the process exits.  All calls share it, so
+// holds it (116,832 bytes) until the process exits.  All calls share it, so
 // calls whose work overlaps on the GPU (different streams, or different host
 // threads on the same device) race and must be serialised by the caller.
 // Each call writes every slot it later reads, so stale contents of an
 // earlier call are never used and nothing needs clearing.
 #include <stdio.h>
 
+#include <atomic>
 #include <chrono>
-#include <mutex>
 #include <thread>
 
 #include "lbm_kernels.cuh"
@@ -35,29 +35,37 @@ namespace {
 // One partial per reduction block plus the final sums.
 constexpr size_t kScratchDoubles = (size_t)(kRedBlocks + 1) * kRedSlots;
 static __device__ __align__(256) double g_reduce_scratch[kScratchDoubles];
+static_assert(sizeof(g_reduce_scratch) == 116832, "the header and the design notes state this size");
+
+// The 32-bit offsets of k_reduce: the last offset a thread forms is below
+// N + kRedThreads.
+static_assert(LBM_NOALLOC_MAX_NODES + kRedThreads - 1 <= 2147483647LL, "node offsets must fit in int");
 
 constexpr int kMaxDevices = 64;
-std::once_flag g_setup_once[kMaxDevices];
-double *g_scratch_dev[kMaxDevices] = {};
-cudaError_t g_setup_status[kMaxDevices] = {};
+std::atomic<double *> g_scratch_dev[kMaxDevices];
 
 // Device address of the scratch array on the current device.  In host code
 // g_reduce_scratch names a host-side shadow, not device memory, so the address
-// must come from cudaGetSymbolAddress, once per device with that device
-// current.
+// must come from cudaGetSymbolAddress with that device current.  Only a
+// successful lookup is kept: a lookup that failed (say, during a stream
+// capture) is tried again by the next call.  Two threads that race on the
+// first lookup store the same address.
 cudaError_t scratch_for_current_device(double **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::call_once(g_setup_once[dev], [dev] {
-        void *p = nullptr;
-        g_setup_status[dev] = cudaGetSymbolAddress(&p, g_reduce_scratch);
-        if (g_setup_status[dev] == cudaSuccess) g_scratch_dev[dev] = (double *)p;
-    });
-    *out = g_scratch_dev[dev];
-    return g_setup_status[dev];
+    double *p = g_scratch_dev[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void *q = nullptr;
+        e = cudaGetSymbolAddress(&q, g_reduce_scratch);
+        if (e != cudaSuccess) return e;
+        p = (double *)q;
+        g_scratch_dev[dev].store(p, std::memory_order_release);
+    }
+    *out = p;
+    return cudaSuccess;
 }
 
 lbm_status fail(lbm_status s, const char *msg)
@@ -85,7 +93,7 @@ extern "C" lbm_status lbm_reduce_noalloc(const void *h, lbm_lattice lattice, lbm
     if (nx < 1 || ny < 1 || nz < 1) return fail(LBM_ERR_ARG, "lbm_reduce_noalloc: lattice sizes must be >= 1");
     const long long N = (long long)nx * ny * nz;
     if (N > (long long)LBM_NOALLOC_MAX_NODES)
-        return fail(LBM_ERR_ARG, "lbm_reduce_noalloc: more than LBM_NOALLOC_MAX_NODES (2^31 - 1) nodes");
+        return fail(LBM_ERR_ARG, "lbm_reduce_noalloc: more than LBM_NOALLOC_MAX_NODES (2^31 - 257) nodes");
     double *scratch = nullptr;
     cudaError_t e = scratch_for_current_device(&scratch);
     if (e != cudaSuccess) return fail_cuda(e, "lbm_reduce_noalloc: scratch set-up");

@@ -20,6 +20,9 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_UNSTABLE, ERR_TIMEOUT = range(7)
 D3Q19, D3Q27 = 19, 27
 F64, F32, F16_SHIFTED, BF16_SHIFTED, F16_SCALED = 0, 1, 2, 3, 4
 DTYPES = {"f64": F64, "f32": F32, "f16": F16_SHIFTED, "bf16": BF16_SHIFTED, "f16s": F16_SCALED}
+# torch element type of each storage type (scaled FP16 stores FP16 of h * 2^12)
+STORAGE_TORCH_DTYPE = {F64: "float64", F32: "float32", F16_SHIFTED: "float16", BF16_SHIFTED: "bfloat16",
+                       F16_SCALED: "float16"}
 PATTERN_AB, PATTERN_AA = 0, 1
 PATTERNS = {"ab": PATTERN_AB, "aa": PATTERN_AA}
 TAG_FLUID, TAG_FORCED, TAG_SOLID, TAG_WALL0, NWALLS = 0, 1, 2, 3, 8
@@ -462,15 +465,35 @@ class Lattice:
 def reduce_noalloc(h, Q: int, dtype, nx: int, ny: int, nz: int, tags=None, force=(0.0, 0.0, 0.0), stream=None):
     """Domain reduction over caller-held device populations without any device
     allocation (``lbm_reduce_noalloc``).  ``h``: CUDA tensor of h = f - w in
-    the storage type, shape (Q, nz, ny, nx); ``tags``: CUDA uint8 tensor or
-    None."""
+    the storage type, shape (Q, nz, ny, nx); ``tags``: CUDA uint8 tensor of
+    nx*ny*nz tags or None.  Both must sit on the current CUDA device, whose
+    static scratch and current stream the library uses: any mismatch of
+    shape, type, count or device raises ValueError before the call."""
     import torch
     lib = load()
     dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
-    if not (isinstance(h, torch.Tensor) and h.is_cuda and h.is_contiguous()):
-        raise TypeError("h must be a contiguous CUDA tensor")
-    if tags is not None and not (isinstance(tags, torch.Tensor) and tags.is_cuda and tags.dtype == torch.uint8):
-        raise TypeError("tags must be a CUDA uint8 tensor")
+    if dt not in STORAGE_TORCH_DTYPE:
+        raise ValueError(f"unknown storage type {dtype!r}")
+    if not isinstance(h, torch.Tensor):
+        raise TypeError("h must be a torch tensor")
+    if tuple(h.shape) != (Q, nz, ny, nx):
+        raise ValueError(f"h has shape {tuple(h.shape)}, expected (Q, nz, ny, nx) = {(Q, nz, ny, nx)}")
+    if h.dtype != getattr(torch, STORAGE_TORCH_DTYPE[dt]):
+        raise ValueError(f"h is {h.dtype}, the storage type needs torch.{STORAGE_TORCH_DTYPE[dt]}")
+    if not h.is_contiguous():
+        raise ValueError("h must be contiguous")
+    if tags is not None:
+        if not isinstance(tags, torch.Tensor) or tags.dtype != torch.uint8:
+            raise ValueError("tags must be a uint8 tensor")
+        if tags.numel() != nx * ny * nz or not tags.is_contiguous():
+            raise ValueError(f"tags must be contiguous with nx*ny*nz = {nx * ny * nz} entries, got {tags.numel()}")
+    for name, t in (("h", h), ("tags", tags)):
+        if t is None:
+            continue
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} is on {t.device}, not on the current device cuda:{torch.cuda.current_device()}")
     p = Params()
     for a in range(3):
         p.force[a] = force[a]

@@ -105,3 +105,27 @@ def test_params_struct_matches_the_header():
     body = re.search(r"typedef struct \{([^}]*)\} lbm_reduction;", text).group(1)
     names = re.findall(r"([a-z_]+)(?:\[[^\]]*\])*\s*;", body)
     assert names == [f[0] for f in lbm.Reduction._fields_]
+
+
+def test_noalloc_reduction_rejects_lattices_beyond_its_bound(lib):
+    """lbm_reduce_noalloc walks node offsets in 32-bit integers: a lattice of
+    LBM_NOALLOC_MAX_NODES + 1 = 2^31 - 256 nodes (the size lbm_create also
+    refuses) is rejected before any device work, so the placeholder pointer
+    is never used."""
+    text = (ROOT / "include" / "lbm.h").read_text()
+    bound = int(re.search(r"#define LBM_NOALLOC_MAX_NODES (\d+)LL", text).group(1))
+    assert bound == (1 << 31) - 257
+    nx, ny, nz = 178481, 47 * 256, 1  # 2^31 - 256 = 256 * 47 * 178481
+    assert nx * ny * nz == bound + 1
+    r = lbm.Reduction()
+    for lattice, dtype in ((19, lbm.F32), (27, lbm.F16_SHIFTED), (19, lbm.F64)):
+        st = lib.lbm_reduce_noalloc(ctypes.c_void_p(256), lattice, dtype, nx, ny, nz, None, None, None,
+                                    ctypes.byref(r))
+        assert st == lbm.ERR_ARG
+        assert b"LBM_NOALLOC_MAX_NODES" in lib.lbm_last_error(None)
+    # lbm_create refuses the same node count (x already a multiple of 32, so
+    # no padding)
+    out = ctypes.c_void_p()
+    assert (32 * 178481) * (8 * 47) == bound + 1
+    assert lib.lbm_create(32 * 178481, 8 * 47, 1, 19, 1, None, None, ctypes.byref(out)) == lbm.ERR_ARG
+    assert not out.value

@@ -134,3 +134,30 @@ def test_tags_must_cover_the_lattice(fake):
     with pytest.raises(ValueError):
         lat.set_tags(np.zeros(10, np.uint8))
     lat.close()
+
+
+def test_reduce_noalloc_checks_its_tensors_before_the_call(fake):
+    """reduce_noalloc hands raw pointers to a library that reads Q*N elements
+    and N tags on the current device: a wrong shape, element type, tag count
+    or device is refused in Python, and the library is never called."""
+    torch = pytest.importorskip("torch")
+    nz, ny, nx = 3, 4, 5
+    good = torch.zeros((19, nz, ny, nx), dtype=torch.float32)
+    cases = [
+        (torch.zeros((19, nz, ny, nx + 1)), None, "shape"),
+        (torch.zeros((27, nz, ny, nx)), None, "shape"),
+        (torch.zeros((19, nz, ny, nx), dtype=torch.float64), None, "float64"),
+        (torch.zeros((19, nz, ny, nx), dtype=torch.float16), None, "float16"),
+        (good, torch.zeros(nx * ny * nz, dtype=torch.int32), "uint8"),
+        (good, torch.zeros(nx * ny * nz - 1, dtype=torch.uint8), "entries"),
+        (good, None, "CUDA"),
+        (torch.zeros((19, nz, nx, ny)).transpose(2, 3), None, "contiguous"),
+    ]
+    for h, tags, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            lbm.reduce_noalloc(h, 19, "f32", nx, ny, nz, tags=tags)
+    with pytest.raises(ValueError, match="bfloat16"):
+        lbm.reduce_noalloc(good, 19, "bf16", nx, ny, nz)
+    with pytest.raises(ValueError, match="unknown storage"):
+        lbm.reduce_noalloc(good, 19, 9, nx, ny, nz)
+    assert not [c for c in fake.calls if c[0] == "lbm_reduce_noalloc"]

@@ -90,11 +90,13 @@ def test_noalloc_without_tags_and_size_limit():
         assert out["n_fluid"] == n ** 3
         assert _close(out["ke"], ref["ke"], 1e-9)
         assert _close(out["mass"], ref["mass"], 1e-12)
-    # sizes beyond the limit are rejected before any device work
+    # sizes beyond the limit (2^31 - 257 nodes) are rejected before any device
+    # work: the bound + 1, and far beyond it
     lib = lbm.load()
     r = lbm.Reduction()
-    st = lib.lbm_reduce_noalloc(ctypes.c_void_p(h.data_ptr()), 19, lbm.F32, 2048, 2048, 1024, None, None, None,
-                                ctypes.byref(r))
-    assert st == lbm.ERR_ARG
+    for dims in ((178481, 47 * 256, 1), (2048, 2048, 1024)):
+        st = lib.lbm_reduce_noalloc(ctypes.c_void_p(h.data_ptr()), 19, lbm.F32, *dims, None, None, None,
+                                    ctypes.byref(r))
+        assert st == lbm.ERR_ARG
     assert b"LBM_NOALLOC_MAX_NODES" in lib.lbm_last_error(None)
     assert lib.lbm_reduce_noalloc(None, 19, lbm.F32, 4, 4, 4, None, None, None, ctypes.byref(r)) == lbm.ERR_ARG
