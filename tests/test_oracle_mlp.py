@@ -159,3 +159,71 @@ def test_closure_features_closed_forms():
     f = ch.step(ch.init_equilibrium(), 15000)
     pxy = ch.closure_features(f)[0, 2:H, 0, 3]
     np.testing.assert_allclose(pxy, -tau * U / (3.0 * H), rtol=2e-3)
+
+
+def _hand_network():
+    """A network whose output follows by hand.  Every pre-activation is an
+    integer of magnitude >= 40 (or exactly a large negative value), where
+    SiLU(z) = z / (1 + e^-z) equals max(z, 0) to within 1e-16 relative, so
+    each layer is a known selection and shift of the previous one:
+      normalised input  xn_k = (x_k - k) / 2,
+      layer 1           unit 3k+1 receives xn_k (bias 0); unit j otherwise
+                        carries only its bias 41 + j,
+      layer 2           unit j receives layer-1 unit (5j + 3) mod 32 (a
+                        permutation, not symmetric, so a transposed W2 shows),
+                        plus bias 40 + j/4,
+      output            y = sum_j w3_j h2_j + b3 with w3_j = (j mod 5 + 1)/16,
+                        b3 = 3; y > 30, where softplus(y) = y to 1e-13;
+      dtau              = out_scale * softplus(y), out_scale = 1/2.
+    Integers below 256 and the chosen fractions are exact in BF16 and FP32,
+    so the BF16-rounding path gives the same value."""
+    W1 = np.zeros((32, 7))
+    b1 = 41.0 + np.arange(32)
+    for k in range(7):
+        W1[3 * k + 1, k] = 1.0
+        b1[3 * k + 1] = 0.0
+    perm = [(5 * j + 3) % 32 for j in range(32)]
+    W2 = np.zeros((32, 32))
+    for j in range(32):
+        W2[j, perm[j]] = 1.0
+    b2 = 40.0 + np.arange(32) / 4.0
+    w3 = (np.arange(32) % 5 + 1) / 16.0
+    b3 = 3.0
+    P = mlp.pack(W1, b1, W2, b2, w3, b3)
+    norm = np.concatenate([np.arange(7.0), np.full(7, 2.0), [0.5, 0.0]])
+    return P, norm, perm, b1, b2, w3, b3
+
+
+def _hand_expected(xn, perm, b1, b2, w3, b3):
+    """The network's value by the selection rules of _hand_network, with exact
+    rational arithmetic."""
+    from fractions import Fraction as F
+    h1 = [F(b1[j]) for j in range(32)]
+    for k in range(7):
+        h1[3 * k + 1] = max(F(xn[k]), F(0))
+    y = sum(F(w3[j]) * (h1[perm[j]] + F(b2[j])) for j in range(32)) + F(b3)
+    return float(F(1, 2) * y)
+
+
+@pytest.mark.parametrize("bf", [False, True])
+def test_network_on_hand_computable_weights(bf):
+    """Pins the forward pass's wiring (which weight multiplies which input,
+    where each bias goes, the normalisation and output scale) on a network
+    whose output is computed by hand, for the numpy oracle and the C oracle."""
+    P, norm, perm, b1, b2, w3, b3 = _hand_network()
+    xns = [np.array([40.0 + 4 * k for k in range(7)]),               # every input passes
+           np.array([-100.0, 50, -100, 50, -100, 50, -100]),           # alternate inputs cut off by SiLU
+           np.array([64.0, -128, 48, -96, 100, -44, 252])]
+    X = np.array([2.0 * xn + np.arange(7) for xn in xns])             # x_k = 2 xn_k + k
+    want = np.array([_hand_expected(xn, perm, b1, b2, w3, b3) for xn in xns])
+    got, cache = mlp.forward(P, norm, X, bf=bf)
+    np.testing.assert_allclose(cache["xn"], np.array(xns), rtol=0, atol=0)
+    np.testing.assert_allclose(got, want, rtol=1e-13)
+    got_c = np.array([oracle.mlp_dtau(P, norm, x, bf16=bf) for x in X])
+    np.testing.assert_allclose(got_c, want, rtol=1e-13)
+    # a plausible wiring mistake moves the result: W2 transposed, or the
+    # first layer's rows and columns exchanged (W1 read as [7][32])
+    W1, _, W2, _, _, _ = mlp.unpack(P)
+    assert abs(mlp.forward(mlp.pack(W1, b1, W2.T, b2, w3, b3), norm, X, bf=bf)[0] - want).max() > 1.0
+    W1_swapped = W1.T.reshape(32, 7)
+    assert abs(mlp.forward(mlp.pack(W1_swapped, b1, W2, b2, w3, b3), norm, X, bf=bf)[0] - want).max() > 1.0
