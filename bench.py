@@ -312,23 +312,70 @@ def replica_throughput(local_ms: float, local_updates: int, dist=None, device: s
     return float(u.item()) / (ms * 1e-3) / 1e9, ms
 
 
-def oracle_glups(n: int = 64, target_s: float = 12.0):
-    """FP64 CPU oracle on the host: periodic 3D TGV, D3Q19, n^3, single thread.
-    Returns (GLUPS, seconds, steps, sample description)."""
+def host_info() -> dict:
+    """Core count, CPU model and architecture of the host."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if not model.isdigit():
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and Path("/proc/cpuinfo").exists():
+        for line in Path("/proc/cpuinfo").read_text().splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    return {"nproc": os.cpu_count(), "cpu_model": model, "arch": platform.machine()}
+
+
+# (Q, n, threads, warm-up steps, timed steps, repeats); threads 0 = every host core
+CPU_PLANS = {
+    # bounded: about a minute of CPU work inside the default bench run
+    "bounded": [(19, 128, 0, 2, 10, 3), (27, 128, 0, 2, 10, 3), (19, 256, 0, 2, 10, 3), (27, 256, 0, 2, 10, 3),
+                (19, 128, 1, 1, 3, 3), (27, 128, 1, 1, 3, 3)],
+    # the full measurement plan: single thread and all cores, 128^3 and 256^3,
+    # D3Q19 and D3Q27, 10 steps after 2 warm-up steps, 3 repeats
+    "full": [(q, n, t, 2, 10, 3) for t in (0, 1) for n in (128, 256) for q in (19, 27)],
+}
+
+
+def oracle_timing(Q: int, n: int, threads: int, warmup: int, steps: int, repeats: int) -> dict:
+    """FP64 CPU oracle on the host: periodic 3D TGV n^3 (u0 = 0.04, Re = 1600),
+    OpenMP over the z planes with the given number of threads.  Returns the
+    mean MLUPS over the repeats, each repeat timing ``steps`` steps."""
     import lbm_inputs as inp
     import oracle
+    cores = oracle.set_threads(threads if threads > 0 else (os.cpu_count() or 1))
     rho, u = inp.tgv3d(n, 0.04)
-    prob = oracle.Problem(19, n, n, n, tau=tgv_tau(n, 0.04, 1600.0))
-    f = prob.init_equilibrium(rho, u)
-    t = time.perf_counter()
-    f = prob.step(f, 1)
-    one = time.perf_counter() - t
-    steps = max(1, int(target_s / max(one, 1e-3)))
-    t = time.perf_counter()
-    prob.step(f, steps)
-    dt = time.perf_counter() - t
-    glups = n ** 3 * steps / dt / 1e9
-    return glups, dt, steps, f"periodic 3D TGV {n}^3 D3Q19 FP64, {steps} steps, single thread"
+    prob = oracle.Problem(Q, n, n, n, tau=tgv_tau(n, 0.04, 1600.0), openmp=True)
+    f = prob.step(prob.init_equilibrium(rho, u), warmup)
+    rates = []
+    for _ in range(repeats):
+        t = time.perf_counter()
+        f = prob.step(f, steps)
+        rates.append(n ** 3 * steps / (time.perf_counter() - t) / 1e6)
+    return {"lattice": f"D3Q{Q}", "n": n, "threads": cores, "mlups": statistics.mean(rates),
+            "mlups_per_core": statistics.mean(rates) / cores, "spread": [min(rates), max(rates)],
+            "steps": steps, "warmup": warmup, "repeats": repeats}
+
+
+def cpu_baseline(plan: str = "bounded") -> dict:
+    """The oracle timed on the host cores (the ``cpu_baseline`` object): the
+    headline value is D3Q19 256^3 on every core, in GLUPS."""
+    rows = [oracle_timing(*cfg) for cfg in CPU_PLANS[plan]]
+    head = next(r for r in rows if r["lattice"] == "D3Q19" and r["n"] == 256 and r["threads"] > 1) \
+        if any(r["threads"] > 1 for r in rows) else rows[0]
+    return {"value": head["mlups"] / 1e3, "unit": UNIT, "cores": head["threads"],
+            "per_core": head["mlups_per_core"] / 1e3, "kind": "oracle",
+            "sample": (f"periodic 3D TGV {head['n']}^3 {head['lattice']} FP64 oracle, {head['steps']} steps after "
+                       f"{head['warmup']} warm-up, mean of {head['repeats']} repeats, {head['threads']} threads "
+                       f"(OpenMP over z planes)"),
+            "host": host_info(), "plan": plan, "table": rows}
 
 
 # ---------------------------------------------------------------------------
@@ -341,8 +388,9 @@ def run_reference(args):
     import lbm_inputs as inp
     import oracle
     n = args.ref_n
+    cores = oracle.set_threads(os.cpu_count() or 1)
     rho, u = inp.tgv3d(n, 0.04)
-    prob = oracle.Problem(19, n, n, n, tau=tgv_tau(n, 0.04, 1600.0))
+    prob = oracle.Problem(19, n, n, n, tau=tgv_tau(n, 0.04, 1600.0), openmp=True)
     f = prob.init_equilibrium(rho, u)
     for _ in range(args.warmup):
         f = prob.step(f, 1)
@@ -351,16 +399,25 @@ def run_reference(args):
         f = prob.step(f, 1)
     dt = time.perf_counter() - t
     glups = n ** 3 * args.steps / dt / 1e9
-    sample = f"periodic 3D TGV {n}^3 (bounded sample of the 512^3 workload), D3Q19 FP64 oracle, single thread"
+    sample = (f"periodic 3D TGV {n}^3 (bounded sample of the 512^3 workload), D3Q19 FP64 oracle, "
+              f"{cores} threads (OpenMP over z planes)")
     line = {
         "impl": "reference", "metric": METRIC, "value": glups, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "tgv3d_512_d3q19_f32", "sample_n": n, "inner_steps": 1},
-        "cpu_baseline": {"value": glups, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": glups, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "host": host_info()},
         "e2e": {"value": glups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_cpu_baseline_only(args):
+    """Only the oracle timing (no GPU): the ``cpu_baseline`` object as one
+    JSON line."""
+    print(json.dumps({"cpu_baseline": cpu_baseline(args.cpu_plan)}), flush=True)
     return 0
 
 
@@ -458,8 +515,7 @@ def run_ours(args):
             torch.cuda.empty_cache()
         errors = error_vs_f64()
         if world == 1:
-            g, dt_s, st, sample = oracle_glups()
-            cpu = {"value": g, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+            cpu = cpu_baseline(args.cpu_plan)
 
     if rank != 0:
         if dist is not None:
@@ -506,13 +562,19 @@ def main(argv=None):
     ap.add_argument("--pattern", default="ab", choices=("ab", "aa"),
                     help="streaming pattern: two arrays (ab) or one array updated in place (aa)")
     ap.add_argument("--inner", type=int, default=20, help="lattice steps per benchmark step (>= 2)")
-    ap.add_argument("--ref-n", type=int, default=64, help="lattice size of the oracle sample")
+    ap.add_argument("--ref-n", type=int, default=128, help="lattice size of the oracle sample (reference arm)")
+    ap.add_argument("--cpu-plan", default="bounded", choices=sorted(CPU_PLANS),
+                    help="oracle timing plan of the CPU baseline")
+    ap.add_argument("--cpu-baseline-only", action="store_true",
+                    help="only time the oracle on the host cores (no GPU) and print the cpu_baseline object")
     ap.add_argument("--no-extras", action="store_true", help="skip variants, error table and CPU baseline")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.inner < 2:
         raise SystemExit("--inner must be >= 2")
+    if args.cpu_baseline_only:
+        return run_cpu_baseline_only(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

@@ -22,6 +22,7 @@ import numpy as np
 _HERE = Path(__file__).resolve().parent
 _SRC = _HERE / "lbm_oracle.c"
 _LIB = _HERE / "_build" / "liblbm_oracle.so"
+_LIB_OMP = _HERE / "_build" / "liblbm_oracle_omp.so"
 
 # Tag values and closure ids of the oracle (its own statement of the tag
 # scheme of Sec. 2.3.2; the CUDA library declares the same values itself).
@@ -32,16 +33,19 @@ F64, F32, F16, BF16, F16_SCALED = 0, 1, 2, 3, 4
 MLP_NPARAM = 32 * 7 + 32 + 32 * 32 + 32 + 32 + 1
 
 
-def build(force: bool = False) -> Path:
-    """Compiles the C oracle into a shared library (plain gcc, no OpenMP)."""
-    _LIB.parent.mkdir(exist_ok=True)
-    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
-        tmp = _LIB.with_suffix(f".{os.getpid()}.tmp")
+def build(force: bool = False, openmp: bool = False) -> Path:
+    """Compiles the C oracle into a shared library: plain gcc (the build the
+    tests use), or with OpenMP over the z planes of a step (the build the
+    CPU baseline times; same arithmetic per node, so the same results)."""
+    lib_path = _LIB_OMP if openmp else _LIB
+    lib_path.parent.mkdir(exist_ok=True)
+    if force or not lib_path.exists() or lib_path.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = lib_path.with_suffix(f".{os.getpid()}.tmp")
         cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-               str(_SRC), "-o", str(tmp), "-lm"]
+               *(["-fopenmp"] if openmp else []), str(_SRC), "-o", str(tmp), "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 class Params(ctypes.Structure):
@@ -80,14 +84,15 @@ class Reduction(ctypes.Structure):
         }
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        _lib = ctypes.CDLL(str(build()))
+def lib(openmp: bool = False):
+    """The plain oracle library, or its OpenMP build (openmp=True)."""
+    if openmp not in _libs:
+        _lib = ctypes.CDLL(str(build(openmp=openmp)))
         D, I, P = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+        _lib.orc_set_threads.argtypes = [I]
         _lib.orc_lattice.argtypes = [I, P, P, P]
         _lib.orc_equilibrium.argtypes = [I, D, P, P]
         _lib.orc_equilibrium.restype = None
@@ -106,7 +111,14 @@ def lib():
         _lib.orc_enstrophy.argtypes = [I, I, I, P, P]
         _lib.orc_enstrophy.restype = D
         _lib.orc_spheres.argtypes = [I, I, I, P, P, I, D, ctypes.c_ubyte, ctypes.c_ubyte, P, P]
-    return _lib
+        _libs[openmp] = _lib
+    return _libs[openmp]
+
+
+def set_threads(n: int) -> int:
+    """Threads of the OpenMP build's steps (n <= 0 keeps the current count);
+    returns the count in use."""
+    return lib(openmp=True).orc_set_threads(int(n))
 
 
 def _ptr(a):
@@ -160,8 +172,10 @@ class Problem:
     def __init__(self, Q: int, nx: int, ny: int, nz: int, tags=None, *, tau: float,
                  force=(0.0, 0.0, 0.0), closure: int = BGK, cs_smag: float = 0.0,
                  wall_u=None, rho_wall: float = 1.0, mlp_params=None, mlp_norm=None,
-                 mlp_bf16: bool = False, trt_magic: float = 3.0 / 16.0, wall_rho_local: bool = False):
+                 mlp_bf16: bool = False, trt_magic: float = 3.0 / 16.0, wall_rho_local: bool = False,
+                 openmp: bool = False):
         self.Q, self.nx, self.ny, self.nz = Q, nx, ny, nz
+        self._lib = lib(openmp=openmp)
         self.tags = None if tags is None else np.ascontiguousarray(tags, dtype=np.uint8).reshape(nz, ny, nx)
         self.p = Params()
         self.p.tau = tau
@@ -191,15 +205,15 @@ class Problem:
         f = np.zeros((self.Q,) + self.shape)
         r = _f64(rho)
         v = _f64(u)
-        lib().orc_init_equilibrium(self.Q, self.nx, self.ny, self.nz, _ptr(r), _ptr(v), _ptr(f))
+        self._lib.orc_init_equilibrium(self.Q, self.nx, self.ny, self.nz, _ptr(r), _ptr(v), _ptr(f))
         return f
 
     def step(self, f: np.ndarray, n: int = 1) -> np.ndarray:
         a = _f64(f).copy()
         b = np.empty_like(a)
         for _ in range(n):
-            rc = lib().orc_step(self.Q, self.nx, self.ny, self.nz, _ptr(self.tags), ctypes.byref(self.p),
-                                _ptr(a), _ptr(b))
+            rc = self._lib.orc_step(self.Q, self.nx, self.ny, self.nz, _ptr(self.tags), ctypes.byref(self.p),
+                                    _ptr(a), _ptr(b))
             if rc != 0:
                 raise ValueError("oracle step rejected its arguments")
             a, b = b, a

@@ -55,6 +55,9 @@
 #include <stddef.h>
 #include <stdint.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ----------------------------------------------------------------------- */
 /* Tags (Sec. 2.3.2: one integer per node selects its behaviour).          */
@@ -384,10 +387,26 @@ static void pull_node(int Q, long long nx, long long ny, long long nz, const uns
     for (int i = 0; i < Q; ++i) f[i] += rho_w * t_wall[i];
 }
 
+/* Worker threads of the z loops below (1 when built without OpenMP).  The
+ * test-suite uses the plain build; the timed CPU baseline may use a build
+ * with OpenMP, where each node's arithmetic is the same, so the populations
+ * are the same bit for bit.  Returns the number of threads now in use. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* One collide-and-stream step in pull form (Sec. 2.3.1-2.3.2): every fluid
  * node pulls its pre-collision set (pull_node), collides, and its
  * post-collision set is written to fout.  Solid and wall nodes are not
- * updated (fout = fin there). */
+ * updated (fout = fin there).  Nodes are independent within a step: with
+ * OpenMP the z planes are shared out among threads. */
 int orc_step(int Q, int nx, int ny, int nz, const unsigned char *tags, const orc_params *p, const double *fin,
              double *fout)
 {
@@ -395,6 +414,7 @@ int orc_step(int Q, int nx, int ny, int nz, const unsigned char *tags, const orc
     if (nx < 1 || ny < 1 || nz < 1 || !(p->tau > 0.5)) return -1;
     if (p->closure == ORC_TRT && !(p->trt_magic > 0.0)) return -1;
     const long long N = (long long)nx * ny * nz;
+#pragma omp parallel for schedule(static)
     for (long long z = 0; z < nz; ++z)
         for (long long y = 0; y < ny; ++y)
             for (long long x = 0; x < nx; ++x) {
@@ -455,6 +475,7 @@ int orc_init_equilibrium(int Q, int nx, int ny, int nz, const double *rho, const
 {
     if (Q != 19 && Q != 27) return -1;
     const long long N = (long long)nx * ny * nz;
+#pragma omp parallel for schedule(static)
     for (long long n = 0; n < N; ++n) {
         double r = rho ? rho[n] : 1.0;
         double v[3] = {0.0, 0.0, 0.0};

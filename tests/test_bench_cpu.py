@@ -69,3 +69,30 @@ def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
     s.start()
     assert s.proc is None and not os.path.exists(s.path)
     assert s.stop() is None
+
+
+def test_cpu_baseline_reports_cores_per_core_rate_and_host(monkeypatch):
+    """The CPU baseline times the oracle on every host core and on one, and
+    reports the threads used, a per-core rate and the host it ran on (here on
+    tiny lattices)."""
+    monkeypatch.setitem(bench.CPU_PLANS, "tiny", [(19, 256, 0, 1, 1, 2), (27, 12, 1, 1, 2, 2)])
+    monkeypatch.setattr(bench, "tgv_tau", lambda n, u0, re: 0.6)
+    import lbm_inputs as inp
+    monkeypatch.setattr(inp, "tgv3d", lambda n, u0, _real=inp.tgv3d: _real(12 if n == 256 else n, u0))
+    import oracle
+    calls = []
+    real_problem = oracle.Problem
+
+    def small_problem(Q, nx, ny, nz, *a, **k):
+        calls.append((Q, nx, k.get("openmp")))
+        m = 12 if nx == 256 else nx
+        return real_problem(Q, m, m, m, *a, **k)
+    monkeypatch.setattr(oracle, "Problem", small_problem)
+    cb = bench.cpu_baseline("tiny")
+    assert cb["kind"] == "oracle" and cb["unit"] == "GLUPS"
+    import os
+    assert cb["cores"] == os.cpu_count()
+    assert cb["value"] > 0 and abs(cb["per_core"] * cb["cores"] - cb["value"]) < 1e-12 * cb["value"] + 1e-15
+    assert set(cb["host"]) == {"nproc", "cpu_model", "arch"} and cb["host"]["nproc"] >= 1
+    assert [r["threads"] for r in cb["table"]][1] == 1
+    assert all(openmp for _, _, openmp in calls)

@@ -54,4 +54,4 @@ def test_bench_uses_the_oracle_only_in_its_baseline_legs():
                 users.add(fn.name)
     top = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))]
     assert not any(isinstance(n, ast.Import) and any(a.name == "oracle" for a in n.names) for n in top)
-    assert users == {"oracle_glups", "run_reference"}
+    assert users == {"oracle_timing", "run_reference"}
