@@ -209,6 +209,20 @@ def recorded_traffic(workload: str):
     return None
 
 
+def recorded_fp64_ops(workload: str):
+    """FP64 instructions per node update of the collide-stream kernel (DFMA,
+    DADD and DMUL counted by ncu), if recorded on the current kernel source."""
+    for p in (ROOT / "profiles").glob("*.md"):
+        text = p.read_text()
+        if f"workload: {workload}" not in text:
+            continue
+        m = re.search(r"fp64_inst_per_node:\s*([0-9.eE+]+)", text)
+        s = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+        if m and s and s.group(1) == kernel_source_hash():
+            return float(m.group(1))
+    return None
+
+
 def measured_peak_hbm():
     p = ROOT / "MEASURED_PEAKS.json"
     if p.exists():
@@ -499,7 +513,7 @@ def run_ours(args):
                                 ("porous400_d3q19", "f16", "bgk", "ab"), ("tgv512_d3q19", "f32", "bgk", "aa"),
                                 ("tgv512_d3q19", "f16", "bgk", "aa"), ("cavity256_d3q19", "f32", "bgk", "aa"),
                                 ("porous400_d3q19", "f32", "bgk", "aa"), ("tgv512_d3q19", "f16s", "bgk", "ab"),
-                                ("tgv512_d3q27", "f16s", "bgk", "ab")):
+                                ("tgv512_d3q27", "f16s", "bgk", "ab"), ("tgv512_d3q19", "f64", "bgk", "ab")):
             if (wl, dt, cl, pat) == (args.workload, args.dtype, args.closure, args.pattern):
                 continue
             v, _, d = make_workload(wl, dt, cl, pat)
@@ -510,6 +524,17 @@ def run_ours(args):
                                        "glups_fluid": d["fluid_nodes"] * args.inner * 5 / (tms * 1e-3) / 1e9,
                                        "kernel_gbs_fluid": 2 * q * SIZE[dt] * d["fluid_nodes"] / (kms * 1e-3) / 1e9}
             variants[d["workload"]]["frac_of_peak"] = variants[d["workload"]]["kernel_gbs_fluid"] / peak
+            if dt == "f64":
+                # FP64 storage collides in FP64: its roof is the FP64 pipe
+                # (DFMA, DADD, DMUL each one instruction), measured live.
+                from paper_2506_09242_gb300 import lbm as _lbm
+                rate = _lbm.fp64_fma_rate()
+                ops = recorded_fp64_ops(f"tgv3d_128_d3q{q}_f64")
+                glups_k = d["fluid_nodes"] / (kms * 1e-3) / 1e9
+                variants[d["workload"]]["alu"] = {
+                    "bound": "fp64", "fp64_flops_measured": rate, "fp64_inst_per_node": ops,
+                    "peak_inst_per_s": rate / 2.0,
+                    "frac": (glups_k * 1e9 * ops / (rate / 2.0)) if ops else None}
             v.close()
             del v
             torch.cuda.empty_cache()

@@ -161,7 +161,8 @@ lbm_status lbm_create(int nx, int ny, int nz, lbm_lattice lattice, lbm_dtype dty
  * reductions and lbm_get_populations read either layout), but lbm_set_tags
  * then returns LBM_ERR_STATE, since the bounced links are stored according
  * to the old tags; take one more step first.  The two-nodes-per-thread
- * kernel of 16-bit storage is A/B only (AA steps use one node per thread).
+ * kernel of 16-bit storage serves A/B steps and the local (even) AA steps;
+ * the odd AA steps use one node per thread.
  * Errors: as lbm_create, and ARG for an unknown pattern. */
 lbm_status lbm_create_ex(int nx, int ny, int nz, lbm_lattice lattice, lbm_dtype dtype, lbm_pattern pattern,
                          const lbm_allocator *alloc, void *stream, lbm_ctx **out);
@@ -378,6 +379,17 @@ lbm_status lbm_coarse_samples(const double *rho, const double *u, int nx, int ny
  * into out[ncomp][Nc]: the mean over each factor^3 block of nodes, coarse
  * cells in x-fastest order.  Asynchronous.  Errors: ARG, CUDA. */
 lbm_status lbm_box_filter(const double *in, int ncomp, int nx, int ny, int nz, int factor, double *out, void *stream);
+
+/* Measurement helper (no counterpart in the paper): the FP64 arithmetic rate
+ * of the current device in operations per second (a fused multiply-add
+ * counts as two), timed with CUDA events over one launch of independent FP64
+ * FMA chains on every SM after a warm-up launch.  It is the arithmetic roof
+ * of the step on LBM_F64 storage, whose collision runs in FP64 (on this
+ * device's FP64 rate that step is bound by arithmetic, not by memory).
+ * stream: cudaStream_t (NULL: legacy default stream).  Allocates and frees
+ * a few kilobytes of device memory; synchronizes.  Errors: ARG (NULL
+ * output), CUDA. */
+lbm_status lbm_fp64_fma_rate(void *stream, double *flops);
 
 /* Library-side sizes: bytes of one population array, x pitch in nodes,
  * number of populations.  Any pointer may be NULL. */

@@ -29,13 +29,12 @@ struct lbm_ctx {
     unsigned long long *census_dev = nullptr;  // LBM_NTAGS + 1 counters
     float *mlp_params = nullptr;  // closure weights (LBM_MLP_NPARAM) + normalisation (LBM_MLP_NNORM)
     void *mlp_image = nullptr;    // the network packed for the collide kernel
-    int *fluid_list = nullptr;    // fluid-node list (mostly-wall lattices), else NULL
-    uint32_t *fluid_mask = nullptr;
+    uint32_t *fluid_list = nullptr;  // fluid-node list (mostly-wall lattices), else NULL
+    uint2 *cwords = nullptr;         // its per-row fluid bitmask table (rows x px/32)
     long long n_list = 0;
     // Compact fluid-only copy of the state used while stepping with the list:
-    // populations cA/cB [Q][nfp] in list order and the neighbour index nbr.
+    // populations cA/cB [Q][nfp] in list order.
     void *cA = nullptr, *cB = nullptr;
-    int *nbr = nullptr;
     long long nfp = 0;
     bool compact_valid = false;  // cA holds the current state
     bool dense_stale = false;    // A lacks the current state (it is in cA)
@@ -58,6 +57,11 @@ struct lbm_ctx {
         unsigned long long version = 0;
     } graphs[4];
     unsigned long long version = 1;
+    // TMA descriptors of the two population arrays (A/B pattern), used by the
+    // learned-closure step; tma_ok is false when they could not be encoded.
+    CUtensorMap tmap[2];
+    const void *tmap_base[2] = {nullptr, nullptr};
+    bool tma_ok = false;
     float *fpart = nullptr;   // per-block FP32 partials of fused step-and-reduce launches
     long long fpart_cap = 0;
     cudaStream_t stream = nullptr;
@@ -139,8 +143,22 @@ Launch make_launch(lbm_ctx *ctx)
     L.general = ctx->general;
     L.closure = ctx->params.closure;
     L.mlp_image = ctx->mlp_image;
-    L.fluid_mask = ctx->fluid_mask;
+    L.tma_A = nullptr;
+    for (int k = 0; k < 2; ++k)
+        if (ctx->tma_ok && ctx->tmap_base[k] == ctx->A) L.tma_A = &ctx->tmap[k];
+    L.cmap.words = ctx->cwords;
+    L.cmap.list = ctx->fluid_list;
+    L.cmap.tags = ctx->tags;
+    L.cmap.nx = ctx->g.nx;
+    L.cmap.ny = ctx->g.ny;
+    L.cmap.nz = ctx->g.nz;
+    L.cmap.nw = ctx->g.px / 32;
+    L.cmap.by_nw = FastDiv((uint32_t)(ctx->g.px / 32));
+    L.cmap.by_ny = FastDiv((uint32_t)ctx->g.ny);
     L.n_list = ctx->n_list;
+    L.moving_walls = false;
+    for (int k = LBM_TAG_WALL0; k < LBM_NTAGS; ++k)
+        if (ctx->census[k]) L.moving_walls = true;
     L.stream = ctx->stream;
     L.aa = ctx->aa;
     L.aa_p = ctx->aa_p;
@@ -193,6 +211,49 @@ bool valid_params(const lbm_params *p, std::string &why)
             if (!isfinite(p->wall_u[k][a])) return why = "wall velocity must be finite", false;
     if (!isfinite(p->rho_wall)) return why = "rho_wall must be finite", false;
     return true;
+}
+
+// cuTensorMapEncodeTiled, looked up through the runtime (no link-time
+// dependence on the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (EncodeTiledFn) nullptr;
+        }
+        return (EncodeTiledFn)p;
+    }();
+    return fn;
+}
+
+// TMA descriptor of one population array: a 4D tensor (x over the padded
+// pitch, y, z, population) copied in boxes of one row of kTmaRow nodes.
+bool encode_population_map(const lbm_ctx *ctx, const void *base, CUtensorMap *map)
+{
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || !base) return false;
+    const cuuint64_t e = ctx->elem;
+    const CUtensorMapDataType type = e == 8   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                     : e == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                              : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    const cuuint64_t dims[4] = {(cuuint64_t)ctx->g.px, (cuuint64_t)ctx->g.ny, (cuuint64_t)ctx->g.nz,
+                                (cuuint64_t)ctx->Q};
+    const cuuint64_t strides[3] = {(cuuint64_t)ctx->g.px * e, (cuuint64_t)ctx->g.px * ctx->g.ny * e,
+                                   (cuuint64_t)ctx->g.sN * e};
+    const cuuint32_t box[4] = {(cuuint32_t)kTmaRow, 1, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(map, type, 4, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -328,19 +389,18 @@ cudaError_t launch_prepare_tags(int Q, const Grid &g, const uint8_t *user, uint8
 // lattice is mostly fluid.  Row counts are scanned on the host.
 static lbm_status build_fluid_list(lbm_ctx *ctx, bool wanted)
 {
-    dev_free(ctx, ctx->fluid_list, sizeof(int) * (size_t)ctx->n_list);
-    dev_free(ctx, ctx->fluid_mask, sizeof(uint32_t) * (size_t)ctx->n_list);
+    const size_t rows = (size_t)ctx->g.nz * ctx->g.ny;
+    const size_t nwords = rows * (size_t)(ctx->g.px / 32);
+    dev_free(ctx, ctx->fluid_list, sizeof(uint32_t) * (size_t)ctx->n_list);
+    dev_free(ctx, ctx->cwords, sizeof(uint2) * nwords);
     dev_free(ctx, ctx->cA, (size_t)ctx->Q * ctx->nfp * ctx->elem);
     dev_free(ctx, ctx->cB, (size_t)ctx->Q * ctx->nfp * ctx->elem);
-    dev_free(ctx, ctx->nbr, sizeof(int) * (size_t)(ctx->Q - 1) * ctx->nfp);
     ctx->fluid_list = nullptr;
-    ctx->fluid_mask = nullptr;
+    ctx->cwords = nullptr;
     ctx->cA = ctx->cB = nullptr;
-    ctx->nbr = nullptr;
     ctx->n_list = ctx->nfp = 0;
     ctx->compact_valid = ctx->dense_stale = false;
     if (!wanted) return LBM_OK;
-    const size_t rows = (size_t)ctx->g.nz * ctx->g.ny;
     Tmp count(ctx, sizeof(int) * rows);
     if (!count.p) return fail(ctx, LBM_ERR_OOM, "fluid-list allocation failed");
     CUDA_TRY(ctx, launch_fluid_count(ctx->g, ctx->tags, (int *)count.p, ctx->stream), "fluid count");
@@ -356,27 +416,21 @@ static lbm_status build_fluid_list(lbm_ctx *ctx, bool wanted)
         total += c;
     }
     if (total == 0) return LBM_OK;
-    ctx->fluid_list = (int *)dev_alloc(ctx, sizeof(int) * (size_t)total);
-    ctx->fluid_mask = (uint32_t *)dev_alloc(ctx, sizeof(uint32_t) * (size_t)total);
+    ctx->fluid_list = (uint32_t *)dev_alloc(ctx, sizeof(uint32_t) * (size_t)total);
+    ctx->cwords = (uint2 *)dev_alloc(ctx, sizeof(uint2) * nwords);
     ctx->n_list = total;
-    if (!ctx->fluid_list || !ctx->fluid_mask) return fail(ctx, LBM_ERR_OOM, "fluid-list allocation failed");
+    if (!ctx->fluid_list || !ctx->cwords) return fail(ctx, LBM_ERR_OOM, "fluid-list allocation failed");
     CUDA_TRY(ctx, cudaMemcpyAsync(count.p, h.data(), sizeof(int) * rows, cudaMemcpyHostToDevice, ctx->stream),
              "fluid start copy");
-    CUDA_TRY(ctx, launch_fluid_scatter(ctx->Q, ctx->g, ctx->tags, (const int *)count.p, ctx->fluid_list, ctx->fluid_mask,
+    CUDA_TRY(ctx, launch_fluid_scatter(ctx->g, ctx->tags, (const int *)count.p, ctx->fluid_list, ctx->cwords,
                                        ctx->stream),
              "fluid scatter");
-    // Compact storage and the neighbour index of every listed node.
+    // Compact storage of the populations in list order.
     ctx->nfp = (total + 255) / 256 * 256;
     const size_t cbytes = (size_t)ctx->Q * ctx->nfp * ctx->elem;
     ctx->cA = dev_alloc(ctx, cbytes);
     ctx->cB = ctx->aa ? nullptr : dev_alloc(ctx, cbytes);
-    ctx->nbr = (int *)dev_alloc(ctx, sizeof(int) * (size_t)(ctx->Q - 1) * ctx->nfp);
-    Tmp index(ctx, sizeof(int) * (size_t)ctx->g.sN);
-    if (!ctx->cA || (!ctx->aa && !ctx->cB) || !ctx->nbr || !index.p)
-        return fail(ctx, LBM_ERR_OOM, "compact storage allocation failed");
-    CUDA_TRY(ctx, launch_build_neighbours(ctx->Q, ctx->g, ctx->tags, ctx->fluid_list, total, ctx->nfp, (int *)index.p,
-                                          ctx->nbr, ctx->stream),
-             "neighbour index");
+    if (!ctx->cA || (!ctx->aa && !ctx->cB)) return fail(ctx, LBM_ERR_OOM, "compact storage allocation failed");
     return sync(ctx);
 }
 
@@ -451,11 +505,10 @@ lbm_status lbm_destroy(lbm_ctx *ctx)
     dev_free(ctx, ctx->census_dev, sizeof(unsigned long long) * (LBM_NTAGS + 1));
     dev_free(ctx, ctx->mlp_params, sizeof(float) * (LBM_MLP_NPARAM + LBM_MLP_NNORM));
     dev_free(ctx, ctx->mlp_image, mlp_image_bytes());
-    dev_free(ctx, ctx->fluid_list, sizeof(int) * (size_t)ctx->n_list);
-    dev_free(ctx, ctx->fluid_mask, sizeof(uint32_t) * (size_t)ctx->n_list);
+    dev_free(ctx, ctx->fluid_list, sizeof(uint32_t) * (size_t)ctx->n_list);
+    dev_free(ctx, ctx->cwords, sizeof(uint2) * (size_t)ctx->g.nz * ctx->g.ny * (size_t)(ctx->g.px / 32));
     dev_free(ctx, ctx->cA, (size_t)ctx->Q * ctx->nfp * ctx->elem);
     dev_free(ctx, ctx->cB, (size_t)ctx->Q * ctx->nfp * ctx->elem);
-    dev_free(ctx, ctx->nbr, sizeof(int) * (size_t)(ctx->Q - 1) * ctx->nfp);
     dev_free(ctx, ctx->fpart, sizeof(float) * kRedSlots * (size_t)ctx->fpart_cap);
     delete ctx;
     return LBM_OK;
@@ -530,6 +583,12 @@ lbm_status lbm_create_ex(int nx, int ny, int nz, lbm_lattice lattice, lbm_dtype 
         return cuda_fail(nullptr, e, "lbm_create");
     }
     ctx->census[LBM_TAG_FLUID] = ctx->g.N;
+    if (!ctx->aa) {  // TMA descriptors for the learned-closure step (its older kernel serves without them)
+        ctx->tmap_base[0] = ctx->A;
+        ctx->tmap_base[1] = ctx->B;
+        ctx->tma_ok = encode_population_map(ctx, ctx->A, &ctx->tmap[0]) &&
+                      encode_population_map(ctx, ctx->B, &ctx->tmap[1]);
+    }
     *out = ctx;
     return LBM_OK;
 }
@@ -643,10 +702,13 @@ static cudaError_t launch_one(lbm_ctx *ctx, bool compact, const void *X, void *Y
     if (compact)
         return by_dtype(ctx->dtype, [&](auto *tag) {
             using S = std::remove_pointer_t<decltype(tag)>;
-            return launch_step_compact<S>(L, ctx->params, X, Y, ctx->nbr, ctx->nfp);
+            return launch_step_compact<S>(L, ctx->params, X, Y, ctx->nfp, nullptr);
         });
     L.A = X;
     L.B = Y;
+    L.tma_A = nullptr;
+    for (int k = 0; k < 2; ++k)
+        if (ctx->tma_ok && ctx->tmap_base[k] == X) L.tma_A = &ctx->tmap[k];
     return by_dtype(ctx->dtype, [&](auto *tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
         return launch_step<S>(L, ctx->params);
@@ -763,6 +825,24 @@ static lbm_status run_steps(lbm_ctx *ctx, int n, bool compact)
     return LBM_OK;
 }
 
+// Whether steps run on the compact fluid-only copy (mostly-wall lattices;
+// the learned closure needs whole warps of x-consecutive nodes and keeps the
+// dense sweep).
+static bool steps_on_compact(const lbm_ctx *ctx) { return ctx->cA && ctx->params.closure != LBM_CLOSURE_MLP; }
+
+// Makes the compact copy hold the current state before steps on it.
+static lbm_status enter_compact(lbm_ctx *ctx)
+{
+    if (!ctx->compact_valid) {
+        CUDA_TRY(ctx, launch_compact_copy(ctx->dtype, ctx->Q, true, ctx->A, ctx->cA, ctx->g.sN, ctx->fluid_list,
+                                          ctx->n_list, ctx->nfp, ctx->stream),
+                 "compact gather");
+        ctx->compact_valid = true;
+    }
+    ctx->dense_stale = true;
+    return LBM_OK;
+}
+
 lbm_status lbm_step(lbm_ctx *ctx, int n)
 {
     if (!ctx) return fail(ctx, LBM_ERR_ARG, "NULL context");
@@ -770,16 +850,9 @@ lbm_status lbm_step(lbm_ctx *ctx, int n)
     if (ctx->params.closure == LBM_CLOSURE_MLP && !ctx->mlp_image)
         return fail(ctx, LBM_ERR_STATE, "MLP closure selected but no weights were set (lbm_set_closure_weights)");
     if (n == 0) return LBM_OK;
-    if (ctx->cA && ctx->params.closure != LBM_CLOSURE_MLP) {
-        // Mostly-wall lattice: step the compact fluid-only copy.
-        if (!ctx->compact_valid) {
-            CUDA_TRY(ctx, launch_compact_copy(ctx->dtype, ctx->Q, true, ctx->A, ctx->cA, ctx->g.sN, ctx->fluid_list,
-                                              ctx->n_list, ctx->nfp, ctx->stream),
-                     "compact gather");
-            ctx->compact_valid = true;
-        }
-        ctx->dense_stale = true;
-        return run_steps(ctx, n, true);
+    if (steps_on_compact(ctx)) {
+        lbm_status st = enter_compact(ctx);
+        return st != LBM_OK ? st : run_steps(ctx, n, true);
     }
     ENSURE_DENSE(ctx);
     ctx->compact_valid = false;
@@ -790,33 +863,44 @@ lbm_status lbm_step_reduce(lbm_ctx *ctx, int n, lbm_reduction *out)
 {
     if (!ctx || !out) return fail(ctx, LBM_ERR_ARG, "NULL argument");
     if (n < 1) return fail(ctx, LBM_ERR_ARG, "n must be >= 1");
-    const bool fusable = !ctx->cA && ctx->dtype != LBM_F64 && ctx->params.closure != LBM_CLOSURE_MLP &&
+    const bool fusable = ctx->dtype != LBM_F64 && ctx->params.closure != LBM_CLOSURE_MLP &&
                          ctx->params.closure != LBM_CLOSURE_STREAM_ONLY;
-    if (!fusable) {  // compact storage, FP64, learned closure, pure streaming: separate passes
+    if (!fusable) {  // FP64, learned closure, pure streaming: separate passes
         lbm_status st = lbm_step(ctx, n);
         return st != LBM_OK ? st : lbm_reduce(ctx, out);
     }
-    ENSURE_DENSE(ctx);
-    ctx->compact_valid = false;
-    lbm_status st = run_steps(ctx, n - 1, false);
+    const bool compact = steps_on_compact(ctx);
+    lbm_status st;
+    if (compact) {
+        st = enter_compact(ctx);
+        if (st != LBM_OK) return st;
+    } else {
+        ENSURE_DENSE(ctx);
+        ctx->compact_valid = false;
+    }
+    st = run_steps(ctx, n - 1, compact);
     if (st != LBM_OK) return st;
     Launch L = make_launch(ctx);
-    const long long nparts = fused_partials(L, ctx->params, ctx->elem);
+    const long long nparts =
+        compact ? (ctx->n_list + kStepThreads - 1) / kStepThreads : fused_partials(L, ctx->params, ctx->elem);
     if (nparts > ctx->fpart_cap) {
         dev_free(ctx, ctx->fpart, sizeof(float) * kRedSlots * (size_t)ctx->fpart_cap);
         ctx->fpart = (float *)dev_alloc(ctx, sizeof(float) * kRedSlots * (size_t)nparts);
         ctx->fpart_cap = ctx->fpart ? nparts : 0;
         if (!ctx->fpart) return fail(ctx, LBM_ERR_OOM, "reduction partials allocation failed");
     }
+    void **X = compact ? &ctx->cA : &ctx->A;
+    void **Y = compact ? (ctx->aa ? &ctx->cA : &ctx->cB) : (ctx->aa ? &ctx->A : &ctx->B);
     CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
                  using S = std::remove_pointer_t<decltype(tag)>;
+                 if (compact) return launch_step_compact<S>(L, ctx->params, *X, *Y, ctx->nfp, ctx->fpart);
                  return launch_step_reduce<S>(L, ctx->params, ctx->fpart);
              }),
              "fused collide-stream-reduce launch");
     if (ctx->aa)
         ctx->aa_p = !ctx->aa_p;
     else
-        std::swap(ctx->A, ctx->B);
+        std::swap(*X, *Y);
     ++ctx->steps;
     CUDA_TRY(ctx, launch_reduce_partials(ctx->fpart, nparts, ctx->partials, ctx->red_out, ctx->stream), "reduce");
     double r[kRedSlots];
@@ -870,16 +954,29 @@ lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *u, int on_device)
 lbm_status lbm_reduce(lbm_ctx *ctx, lbm_reduction *out)
 {
     if (!ctx || !out) return fail(ctx, LBM_ERR_ARG, "NULL argument");
-    ENSURE_DENSE(ctx);
-    const long long total = (long long)ctx->g.nz * ctx->g.ny * ctx->g.px;
-    long long nb = (total + kRedThreads - 1) / kRedThreads;
-    if (nb > kRedBlocks) nb = kRedBlocks;
     Launch L = make_launch(ctx);
-    CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
-                 using S = std::remove_pointer_t<decltype(tag)>;
-                 return launch_reduce<S>(L, ctx->params, ctx->partials, (int)nb, ctx->red_out);
-             }),
-             "reduce");
+    if (ctx->cA && ctx->compact_valid) {
+        // The compact copy holds the current state: reduce over the fluid
+        // nodes there, without writing the dense arrays back.
+        long long nb = (ctx->n_list + kRedThreads - 1) / kRedThreads;
+        if (nb > kRedBlocks) nb = kRedBlocks;
+        CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
+                     using S = std::remove_pointer_t<decltype(tag)>;
+                     return launch_reduce_compact<S>(L, ctx->params, ctx->cA, ctx->nfp, ctx->partials, (int)nb,
+                                                     ctx->red_out);
+                 }),
+                 "reduce");
+    } else {
+        ENSURE_DENSE(ctx);
+        const long long total = (long long)ctx->g.nz * ctx->g.ny * ctx->g.px;
+        long long nb = (total + kRedThreads - 1) / kRedThreads;
+        if (nb > kRedBlocks) nb = kRedBlocks;
+        CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
+                     using S = std::remove_pointer_t<decltype(tag)>;
+                     return launch_reduce<S>(L, ctx->params, ctx->partials, (int)nb, ctx->red_out);
+                 }),
+                 "reduce");
+    }
     double r[kRedSlots];
     CUDA_TRY(ctx, cudaMemcpyAsync(r, ctx->red_out, sizeof r, cudaMemcpyDeviceToHost, ctx->stream), "reduce copy");
     lbm_status s = sync(ctx);

@@ -1,5 +1,7 @@
 // lbm_diag.cu -- kernels of the porous-medium generator and of the enstrophy
 // diagnostic (storage-type independent; the host side is in lbm_api.cu).
+#include <stdio.h>
+
 #include "lbm_kernels.cuh"
 
 namespace lbm {
@@ -149,4 +151,72 @@ cudaError_t launch_enstrophy(bool fp64, int nx, int ny, int nz, const double *u,
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// FP64 arithmetic roof: the rate of independent FP64 fused multiply-adds on
+// every SM (the step on FP64 storage runs all of its arithmetic in FP64).
+// Each thread advances kFmaChains independent recurrences a <- a * b + c,
+// so the FMA pipe, not latency, sets the time.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kFmaChains = 8;
+constexpr int kFmaIters = 2048;
+constexpr int kFmaThreads = 256;
+
+__global__ void __launch_bounds__(kFmaThreads) k_fp64_fma(double b, double c, double *__restrict__ sink)
+{
+    double a[kFmaChains];
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) a[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+    for (int it = 0; it < kFmaIters; ++it)
+#pragma unroll
+        for (int k = 0; k < kFmaChains; ++k) a[k] = fma(a[k], b, c);
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) s += a[k];
+    if (threadIdx.x == 0) sink[blockIdx.x] = s;  // keeps the chains live
+}
+}  // namespace
+
+void set_last_error_global(const char *msg);  // defined in lbm_api.cu
+
 }  // namespace lbm
+
+extern "C" lbm_status lbm_fp64_fma_rate(void *stream, double *flops)
+{
+    using namespace lbm;
+    if (!flops) {
+        set_last_error_global("lbm_fp64_fma_rate: NULL output");
+        return LBM_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double *sink = nullptr;
+    float ms = 0.f;
+    const int blocks_per_sm = 8;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = sms * blocks_per_sm;
+    if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(double) * (size_t)blocks);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) {
+        k_fp64_fma<<<blocks, kFmaThreads, 0, s>>>(0.999999, 1e-7, sink);  // warm-up
+        cudaEventRecord(e0, s);
+        k_fp64_fma<<<blocks, kFmaThreads, 0, s>>>(0.999999, 1e-7, sink);
+        cudaEventRecord(e1, s);
+        e = cudaEventSynchronize(e1);
+    }
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (sink) cudaFree(sink);
+    if (e != cudaSuccess) {
+        char buf[256];
+        snprintf(buf, sizeof buf, "lbm_fp64_fma_rate: %s", cudaGetErrorString(e));
+        set_last_error_global(buf);
+        return LBM_ERR_CUDA;
+    }
+    *flops = 2.0 * kFmaChains * (double)kFmaIters * kFmaThreads * blocks / (ms * 1e-3);
+    return LBM_OK;
+}

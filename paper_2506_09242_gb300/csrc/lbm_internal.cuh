@@ -3,6 +3,7 @@
 // launcher declarations implemented once per storage type.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -101,11 +102,51 @@ template <> struct Store<h16s> {
     static __device__ __forceinline__ T rt(T v) { return __half2float(__float2half_rn(v * kF16sUp)) * kF16sDown; }
 };
 
-// Fluid-node list (lattices that are mostly wall): link mask of each listed
-// node, bit i set when the pull source of direction i is SOLID or WALL.
-constexpr uint32_t kListForced = 1u << 30;   // the node carries the body force
-constexpr uint32_t kListAnyWall = 1u << 31;  // some source is a moving wall
-constexpr double kListWallFraction = 0.3;    // use the list above this wall fraction
+// Fluid-node list (lattices that are mostly wall): one 32-bit entry per
+// listed node, its padded offset (z ny + y) px + x with bit 31 set when the
+// node carries the body force (offsets stay below 2^31 - 256).
+constexpr uint32_t kListForced = 1u << 31;
+constexpr uint32_t kListOffset = kListForced - 1u;
+constexpr double kListWallFraction = 0.3;  // use the list above this wall fraction
+
+// Division by a divisor fixed at launch (Granlund & Montgomery, "Division by
+// invariant integers using multiplication", 1994, Sec. 4): with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, the quotient of
+// n < 2^31 is (umulhi(m, n) + n) >> l (the sum stays below 2^32).
+struct FastDiv {
+    uint32_t d = 1, m = 1;
+    int l = 0;
+    FastDiv() = default;
+    explicit FastDiv(uint32_t div) : d(div)
+    {
+        l = 0;
+        while ((1ull << l) < div) ++l;
+        m = (uint32_t)(((1ull << 32) * ((1ull << l) - div)) / div + 1ull);
+    }
+    __host__ __device__ __forceinline__ uint32_t div(uint32_t n) const
+    {
+#ifdef __CUDA_ARCH__
+        return (__umulhi(m, n) + n) >> l;
+#else
+        return (uint32_t)((((uint64_t)m * n >> 32) + n) >> l);
+#endif
+    }
+};
+
+// Addressing of the compact fluid-only storage without a stored neighbour
+// index: per row of the padded lattice and per 32 x positions one entry
+// {fluid bits, list position of the word's first fluid node}, so the list
+// position of a fluid node (xs, row) is
+//   words[row nw + xs/32].y + popc(words[..].x & ((1 << xs%32) - 1)).
+// The table holds 8 bytes per 32 nodes (16 MB for 400^3); the step reads it
+// through L2, and from HBM only the populations and one list entry per node.
+struct CompactMap {
+    const uint2 *words;     // [rows][nw]
+    const uint32_t *list;   // [n_list]: offset | kListForced
+    const uint8_t *tags;    // internal padded tags (read for moving-wall sources)
+    int nx, ny, nz, nw;     // nw = px / 32 words per row
+    FastDiv by_nw, by_ny;   // row = (offset / 32) / nw, z = row / ny
+};
 
 // Internal tag byte: the user tag in the low 7 bits, bit 7 set on fluid
 // nodes that have a SOLID or WALL node among their Q neighbours.
@@ -152,8 +193,10 @@ struct Launch {
     bool general;             // tags present (not all FLUID)
     int closure;
     const void *mlp_image;    // device packed closure network (MlpSmem, closure 2)
-    const uint32_t *fluid_mask;  // per listed fluid node: kListForced (compact step)
-    long long n_list;            // number of listed fluid nodes
+    const CUtensorMap *tma_A; // TMA descriptor of the populations at A (host memory), or NULL
+    CompactMap cmap;          // compact fluid-only storage (mostly-wall lattices)
+    long long n_list;         // number of listed fluid nodes
+    bool moving_walls;        // some node carries a moving-wall tag
     cudaStream_t stream;
     bool aa = false;    // AA pattern: one array, A == B
     bool aa_p = false;  // AA state in layout P (the next step is an even one)
@@ -167,9 +210,16 @@ template <typename S> cudaError_t launch_step(const Launch &L, const lbm_params 
 // state, kRedSlots floats per block (cudaErrorNotSupported for FP64 storage
 // and for closures without a fused variant).
 template <typename S> cudaError_t launch_step_reduce(const Launch &L, const lbm_params &p, float *partials);
+// One step on compact storage; with partials (FP32 compute; BGK,
+// Smagorinsky, TRT) it also writes the block reduction partials of the new
+// state, kRedSlots floats per block of kStepThreads listed nodes.
 template <typename S>
-cudaError_t launch_step_compact(const Launch &L, const lbm_params &p, const void *Ac, void *Bc, const int *nbr,
-                                long long nfp);
+cudaError_t launch_step_compact(const Launch &L, const lbm_params &p, const void *Ac, void *Bc, long long nfp,
+                                float *partials);
+// The domain reduction over the compact copy of the state.
+template <typename S>
+cudaError_t launch_reduce_compact(const Launch &L, const lbm_params &p, const void *Ac, long long nfp,
+                                  double *partials, int nblocks, double *out);
 template <typename S>
 cudaError_t launch_reduce(const Launch &L, const lbm_params &p, double *partials, int nblocks, double *out);
 template <typename S>
@@ -180,8 +230,11 @@ template <typename S> cudaError_t launch_get_pop(const Launch &L, int i, double 
 template <typename S> cudaError_t launch_step_aa(const Launch &L, const lbm_params &p);
 template <typename S> cudaError_t launch_step_reduce_aa(const Launch &L, const lbm_params &p, float *partials);
 template <typename S>
-cudaError_t launch_step_compact_aa(const Launch &L, const lbm_params &p, const void *Ac, void *Bc, const int *nbr,
-                                   long long nfp);
+cudaError_t launch_step_compact_aa(const Launch &L, const lbm_params &p, const void *Ac, void *Bc, long long nfp,
+                                   float *partials);
+template <typename S>
+cudaError_t launch_reduce_compact_aa(const Launch &L, const lbm_params &p, const void *Ac, long long nfp,
+                                     double *partials, int nblocks, double *out);
 template <typename S>
 cudaError_t launch_reduce_aa(const Launch &L, const lbm_params &p, double *partials, int nblocks, double *out);
 template <typename S> cudaError_t launch_moments_aa(const Launch &L, const lbm_params &p, double *rho, double *u);
@@ -202,12 +255,10 @@ cudaError_t launch_reduce_partials(const float *partials, long long n, double *c
 
 // Fluid-node list (lbm_sparse.cu).
 cudaError_t launch_fluid_count(const Grid &g, const uint8_t *tags, int *count, cudaStream_t s);
-cudaError_t launch_fluid_scatter(int Q, const Grid &g, const uint8_t *tags, const int *start, int *list,
-                                 uint32_t *mask, cudaStream_t s);
-cudaError_t launch_build_neighbours(int Q, const Grid &g, const uint8_t *tags, const int *list, long long n,
-                                    long long nfp, int *index, int *nbr, cudaStream_t s);
+cudaError_t launch_fluid_scatter(const Grid &g, const uint8_t *tags, const int *start, uint32_t *list, uint2 *words,
+                                 cudaStream_t s);
 cudaError_t launch_compact_copy(lbm_dtype dtype, int Q, bool to_compact, const void *src, void *dst, long long sN,
-                                const int *list, long long n, long long nfp, cudaStream_t s);
+                                const uint32_t *list, long long n, long long nfp, cudaStream_t s);
 
 // Porous-medium generator and enstrophy diagnostic (lbm_diag.cu).
 cudaError_t launch_sphere_cover(int nx, int ny, int nz, const int *centres, const double *radii, int n,

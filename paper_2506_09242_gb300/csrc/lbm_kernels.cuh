@@ -447,29 +447,16 @@ template <typename T> struct Macro {
     T drho, rho, inv, ux, uy, uz, Gx, Gy, Gz;
 };
 
-// rho = 1 + sum h, j = sum c h (+ rho g / 2 on a forced node), u = j / rho.
-template <int Q, typename T, bool FIRST_TERM = true>
+// rho = 1 + sum h, j = sum c h (+ rho g / 2 on a forced node), u = j / rho;
+// every sum starts from its first term (no addition of zero).
+template <int Q, typename T>
 __device__ __forceinline__ Macro<T> node_macros(const T (&h)[Q], bool forced, const KParams<T> &p)
 {
     Macro<T> m;
-    T drho, jx, jy, jz;
-    if constexpr (FIRST_TERM) {
-        drho = h[0];
-        jx = csum<Q, T, 0>(h);
-        jy = csum<Q, T, 1>(h);
-        jz = csum<Q, T, 2>(h);
+    T drho = h[0];
+    T jx = csum<Q, T, 0>(h), jy = csum<Q, T, 1>(h), jz = csum<Q, T, 2>(h);
 #pragma unroll
-        for (int i = 1; i < Q; ++i) drho += h[i];
-    } else {
-        drho = jx = jy = jz = T(0);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            drho += h[i];
-            if (cvel(i, 0)) jx += cvel(i, 0) > 0 ? h[i] : -h[i];
-            if (cvel(i, 1)) jy += cvel(i, 1) > 0 ? h[i] : -h[i];
-            if (cvel(i, 2)) jz += cvel(i, 2) > 0 ? h[i] : -h[i];
-        }
-    }
+    for (int i = 1; i < Q; ++i) drho += h[i];
     m.drho = drho;
     m.rho = T(1) + drho;
     m.Gx = m.Gy = m.Gz = T(0);
@@ -521,7 +508,7 @@ __device__ __forceinline__ void pi_neq(const T (&h)[Q], const Macro<T> &m, T (&p
 // equilibria h_eq = S +- A share the even part S = w (drho + rho (4.5 (c.u)^2
 // - 1.5 u^2)) and differ in the sign of the odd part A = 3 w rho (c.u), and
 // Guo's source F = w [3 (c - u) + 9 (c.u) c] . G splits the same way.
-template <int Q, typename T, bool PAIRED = true>
+template <int Q, typename T>
 __device__ __forceinline__ void relax(T (&h)[Q], const Macro<T> &m, T omega, bool forced)
 {
     const T usq15 = T(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
@@ -533,14 +520,12 @@ __device__ __forceinline__ void relax(T (&h)[Q], const Macro<T> &m, T omega, boo
         if (forced) h0 += cf * (w0 * (T(-3) * uG));
         h[0] = h0;
     }
-    if constexpr ((Q == 27 && sizeof(T) == 4) || !PAIRED) {
+    if constexpr (Q == 27 && sizeof(T) == 4) {
         // One direction at a time with the full dot products: the same
         // algebra as the paired form below.  For D3Q27 in FP32 the 16-bit
         // two-node kernel compiles this form to 80 registers (the paired form
-        // to 86-90), which keeps six blocks per SM resident instead of five;
-        // the A/B compact kernel (!PAIRED), bound by the latency of its
-        // gathers, is fastest with it as well (measured).  FP64 compute,
-        // bound by the FP64 rate, takes the paired form.
+        // to 86-90), which keeps six blocks per SM resident instead of five.
+        // FP64 compute, bound by the FP64 rate, takes the paired form.
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
@@ -613,18 +598,13 @@ __device__ __forceinline__ void relax_trt(T (&h)[Q], const Macro<T> &m, T wp, T 
 }
 
 // Returns the density and velocity the collision used (mass and momentum
-// invariants of the new state).
-// LEAN selects the paired relaxation and first-term moment sums (fewer
-// instructions, for the issue-bound kernels).  The A/B step on compact
-// storage, bound by the latency of its gathers, takes the one-direction-at-a-
-// time form: 48 registers instead of 64 (28.9 against 20.2 fluid GLUPS on a
-// 400^3 porous medium); its AA steps are faster with the lean form.  The two
-// forms differ only in rounding.
-template <int Q, typename T, int CLOSURE, bool LEAN = true>
+// invariants of the new state).  Every step kernel collides with this
+// function, so the same pulled set gives the same bits in all of them.
+template <int Q, typename T, int CLOSURE>
 __device__ __forceinline__ Macro<T> collide_node(T (&h)[Q], bool forced, const KParams<T> &p)
 {
     if (CLOSURE == LBM_CLOSURE_STREAM_ONLY) return Macro<T>{};
-    const Macro<T> m = node_macros<Q, T, LEAN>(h, forced, p);
+    const Macro<T> m = node_macros<Q, T>(h, forced, p);
     if (CLOSURE == LBM_CLOSURE_TRT) {
         relax_trt<Q, T>(h, m, p.omega, p.omega_minus, forced);
         return m;
@@ -637,7 +617,7 @@ __device__ __forceinline__ Macro<T> collide_node(T (&h)[Q], bool forced, const K
         const T te = T(0.5) * (p.tau + sqrt(p.tau * p.tau + p.smag18 * sqrt(T(2) * pp) * m.inv));
         omega = T(1) / te;
     }
-    relax<Q, T, LEAN>(h, m, omega, forced);
+    relax<Q, T>(h, m, omega, forced);
     return m;
 }
 
@@ -712,119 +692,260 @@ __global__ void __launch_bounds__(kStepThreads)
     if constexpr (REDUCE) block_partial_f32(ns, partials + linear_block() * kRedSlots);
 }
 
+// ---------------------------------------------------------------------------
+// Compact fluid-only storage (lattices that are mostly wall, e.g. porous
+// media): one thread per listed fluid node t, populations A[Q][nfp] in list
+// order.  The list position of each pull source is found from the per-row
+// fluid bitmask table (CompactMap): the node's coordinates come from its list
+// entry, and the source x - c_i is fluid when its bit is set, at list
+// position base + popc(bits below it).  So from HBM a step reads the
+// populations and one 4-byte list entry per node; the 8-byte table entries
+// (8 bytes per 32 lattice nodes) are shared by the nodes of nine rows and
+// stay in L2.
+// ---------------------------------------------------------------------------
+struct CompactNode {
+    int xs[3];          // x - 1, x, x + 1 (wrapped)
+    int wx[3];          // their words in a row: xs / 32
+    uint32_t bm[3];     // their bits in the word: 1 << (xs % 32)
+    int rw[3][3];       // rw[dy+1][dz+1] = row(z + dz, y + dy) * nw (wrapped)
+    bool forced;
+
+    __device__ __forceinline__ void init(const CompactMap &cm, uint32_t entry)
+    {
+        forced = (entry & kListForced) != 0u;
+        const uint32_t off = entry & kListOffset;
+        const uint32_t row = cm.by_nw.div(off >> 5);
+        const int x = (int)(off - row * 32u * (uint32_t)cm.nw);
+        const uint32_t z = cm.by_ny.div(row);
+        const int y = (int)(row - z * (uint32_t)cm.ny), zi = (int)z;
+        xs[0] = x == 0 ? cm.nx - 1 : x - 1;
+        xs[1] = x;
+        xs[2] = x == cm.nx - 1 ? 0 : x + 1;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            wx[k] = xs[k] >> 5;
+            bm[k] = 1u << (xs[k] & 31);
+        }
+        const int ys[3] = {y == 0 ? cm.ny - 1 : y - 1, y, y == cm.ny - 1 ? 0 : y + 1};
+        const int zs[3] = {zi == 0 ? cm.nz - 1 : zi - 1, zi, zi == cm.nz - 1 ? 0 : zi + 1};
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) rw[a][b] = (zs[b] * cm.ny + ys[a]) * cm.nw;
+    }
+
+    // Code of the pull source x - c_i of direction i: its list position when
+    // it is fluid, -1 for a SOLID node, -2 - k for moving wall k (WALLS: the
+    // lattice has moving walls, whose tag byte is then read; without them
+    // every non-fluid node is SOLID).
+    template <bool WALLS>
+    __device__ __forceinline__ int code(const CompactMap &cm, int i) const
+    {
+        const int k = 1 - cvel(i, 0);
+        const int r = rw[1 - cvel(i, 1)][1 - cvel(i, 2)];
+        const uint2 e = __ldg(cm.words + (uint32_t)(r + wx[k]));
+        if (e.x & bm[k]) return (int)(e.y + __popc(e.x & (bm[k] - 1u)));
+        if constexpr (!WALLS) {
+            return -1;
+        } else {
+            const unsigned ts = cm.tags[(uint32_t)(r * 32 + xs[k])] & kTagMask;  // row * px = (row * nw) * 32
+            return ts == LBM_TAG_SOLID ? -1 : -2 - (int)(ts - LBM_TAG_WALL0);
+        }
+    }
+};
+
 // The local-density wall on compact storage: h holds the bounced links
-// without their wall terms; adds rho0 / (1 - s) times each term.
+// without their wall terms; adds rho0 / (1 - s) times each term.  sv: the
+// source codes of the node's links.
 template <int Q, typename T>
-__device__ __forceinline__ void compact_local_wall(T (&h)[Q], const int *__restrict__ nbr, long long t, long long nfp,
-                                                   uint32_t m, const KParams<T> &p)
+__device__ __forceinline__ void compact_local_wall(T (&h)[Q], const int (&sv)[Q], const KParams<T> &p)
 {
     T s = T(0);
+    bool any = false;
 #pragma unroll
     for (int i = 1; i < Q; ++i)
-        if ((m >> i) & 1u) {
-            const int k = __ldg(nbr + (long long)(i - 1) * nfp + t);
-            if (k < -1) s += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - k), p);
+        if (sv[i] < -1) {
+            s += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - sv[i]), p);
+            any = true;
         }
+    if (!any) return;
     const T rw = local_wall_rho<Q, T>(h, s);
 #pragma unroll
     for (int i = 1; i < Q; ++i)
-        if ((m >> i) & 1u) {
-            const int k = __ldg(nbr + (long long)(i - 1) * nfp + t);
-            if (k < -1) h[i] += rw * wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - k), p);
-        }
+        if (sv[i] < -1) h[i] += rw * wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - sv[i]), p);
 }
 
-// ---------------------------------------------------------------------------
-// The step on compact fluid-only storage (lattices that are mostly wall, e.g.
-// porous media): one thread per fluid node, populations A[Q][nfp] in the
-// order of the fluid-node list, and the neighbour index nbr[i-1][k] of each
-// pull source (its list position, -1 for SOLID, -2 - w for moving wall w), so
-// every load and store touches fluid data only and a bounced link costs the
-// same single load as a streamed one.  (The learned closure needs whole warps
-// of consecutive nodes and keeps the dense sweep.)
-// ---------------------------------------------------------------------------
-// LOCAL: the local-density wall (p.wall_local); a separate instantiation,
-// since its second pass over the neighbour index keeps the first pass's 18
-// to 26 indices live and costs the kernel 17 to 38 registers.
-template <int Q, typename S, int CLOSURE, int PAT = kPatAB, bool LOCAL = false>
-__global__ void __launch_bounds__(kStepThreads)
-    k_collide_stream_compact(const S *__restrict__ A, S *__restrict__ B, const int *__restrict__ nbr,
-                             const uint32_t *__restrict__ mask, long long n, long long nfp,
-                             KParams<typename Store<S>::T> p)
+// The fused reduction's share of one node (FP32 compute): the density and
+// velocity the collision used where the storage is FP32, otherwise those of
+// the post-collision set rounded to the storage type.
+template <int Q, typename S>
+__device__ __forceinline__ void compact_reduce_add(const typename Store<S>::T (&h)[Q],
+                                                   const Macro<typename Store<S>::T> &m, bool forced,
+                                                   const KParams<typename Store<S>::T> &p, NodeSums &ns)
+{
+    using T = typename Store<S>::T;
+    static_assert(sizeof(T) == 4, "fused reductions are FP32-compute only");
+    if constexpr (sizeof(S) == sizeof(T)) {
+        const float u[3] = {m.ux, m.uy, m.uz};
+        ns.add(m.drho, u);
+    } else {
+        T d, u[3];
+        stored_moments<Q, S>(h, forced, p, d, u);
+        ns.add(d, u);
+    }
+}
+
+// One listed node of the compact step.  I: the index type of the compact
+// arrays, uint32_t when Q nfp < 2^32 (one 32-bit multiply-add per address),
+// long long otherwise.
+//   PAT:    AB (A -> B), or an odd or even AA step in place in B;
+//   LOCAL:  the local-density wall (p.wall_local), a separate instantiation
+//           since keeping all source codes live costs registers;
+//   WALLS:  the lattice has moving walls (their tags are read);
+//   REDUCE: add the new state's density and velocity to ns (FP32 compute).
+template <int Q, typename S, typename I, int CLOSURE, int PAT, bool LOCAL, bool WALLS, bool REDUCE>
+__device__ __forceinline__ void compact_node(const S *__restrict__ A, S *__restrict__ B, const CompactMap &cm, I t,
+                                             I nfp, const KParams<typename Store<S>::T> &p, NodeSums &ns)
 {
     using T = typename Store<S>::T;
     using St = Store<S>;
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= n) return;
+    CompactNode nd;
+    nd.init(cm, __ldg(cm.list + t));
     T h[Q];
+    Macro<T> m;
     if constexpr (PAT == kPatAB && !LOCAL) {
+        // AB: h_i = A[i][s_i], a bounced link A[opp(i)][t] (+ Ladd's term).
+        // All source codes first, then all population loads: the table
+        // loads, then the population loads, are in flight together (measured
+        // on a 400^3 porous medium: 1.3x (FP32) to 1.9x (FP16) faster than
+        // loading each population right after its code).
+        int sv[Q];
+        sv[0] = 0;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) sv[i] = nd.code<WALLS>(cm, i);
         h[0] = St::ld(A + t);
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            const int s = __ldg(nbr + (long long)(i - 1) * nfp + t);
-            const long long a = s >= 0 ? (long long)i * nfp + s : (long long)opp(i) * nfp + t;
+            const int s = sv[i];
+            const I a = s >= 0 ? (I)i * nfp + (I)s : (I)opp(i) * nfp + t;
             T v = St::ld(A + a);
-            if (s < -1) v += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - s), p);
+            if (WALLS && s < -1) v += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - s), p);
             h[i] = v;
         }
-        collide_node<Q, T, CLOSURE, false>(h, (__ldg(mask + t) & kListForced) != 0u, p);
+        m = collide_node<Q, T, CLOSURE>(h, nd.forced, p);
+        if constexpr (REDUCE) compact_reduce_add<Q, S>(h, m, nd.forced, p, ns);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) St::st(B + (long long)i * nfp + t, h[i]);
+        for (int i = 0; i < Q; ++i) St::st(B + ((I)i * nfp + t), h[i]);
         return;
     }
     const S *F = PAT == kPatAB ? A : B;  // AA: in place through B
-    const uint32_t m = __ldg(mask + t);
     if constexpr (PAT == kPatAAEven) {
         // Local reads (layout P); links from a moving wall add Ladd's term.
 #pragma unroll
-        for (int i = 0; i < Q; ++i) h[i] = St::ldc(F + (long long)i * nfp + t);
-        if (m & kListAnyWall) {
+        for (int i = 0; i < Q; ++i) h[i] = St::ldc(F + ((I)i * nfp + t));
+        if constexpr (WALLS) {
+            int sv[Q];
+            sv[0] = 0;
+#pragma unroll
+            for (int i = 1; i < Q; ++i) sv[i] = nd.code<WALLS>(cm, i);
             if (LOCAL) {
-                compact_local_wall<Q, T>(h, nbr, t, nfp, m, p);
+                compact_local_wall<Q, T>(h, sv, p);
             } else {
 #pragma unroll
                 for (int i = 1; i < Q; ++i)
-                    if ((m >> i) & 1u) {
-                        const int s = __ldg(nbr + (long long)(i - 1) * nfp + t);
-                        if (s < -1) h[i] += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - s), p);
-                    }
+                    if (sv[i] < -1) h[i] += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - sv[i]), p);
             }
         }
-        collide_node<Q, T, CLOSURE>(h, (m & kListForced) != 0u, p);
+        m = collide_node<Q, T, CLOSURE>(h, nd.forced, p);
+        if constexpr (REDUCE) compact_reduce_add<Q, S>(h, m, nd.forced, p, ns);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) St::st(B + (long long)opp(i) * nfp + t, h[i]);
+        for (int i = 0; i < Q; ++i) St::st(B + ((I)opp(i) * nfp + t), h[i]);
     } else {
-        // AB: h_i = A[i][s_i]; odd AA: h_i = F[opp(i)][s_i] and f*_i goes to
-        // F[i][s_opp(i)], the list position of x + c_i.  A bounced link reads
-        // (and, in AA, writes back) the node's own slot.
+        // AB (local-density wall): h_i = A[i][s_i]; odd AA: h_i = F[opp(i)][s_i]
+        // and f*_i goes to F[i][s_opp(i)], the list position of x + c_i.  A
+        // bounced link reads (and, in AA, writes back) the node's own slot.
         int sv[Q];
         sv[0] = 0;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) sv[i] = nd.code<WALLS>(cm, i);
         h[0] = pop_ld<S, PAT>(F + t);
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            const int s = __ldg(nbr + (long long)(i - 1) * nfp + t);
-            sv[i] = s;
+            const int s = sv[i];
             const int slot = PAT == kPatAB ? i : opp(i);
-            const long long a = s >= 0 ? (long long)slot * nfp + s
-                                       : (long long)(PAT == kPatAB ? opp(i) : i) * nfp + t;
+            const I a = s >= 0 ? (I)slot * nfp + (I)s : (I)(PAT == kPatAB ? opp(i) : i) * nfp + t;
             T v = pop_ld<S, PAT>(F + a);
-            if (s < -1 && !LOCAL) v += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - s), p);
+            if (WALLS && s < -1 && !LOCAL) v += wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - s), p);
             h[i] = v;
         }
-        if (LOCAL && (m & kListAnyWall)) compact_local_wall<Q, T>(h, nbr, t, nfp, m, p);
-        collide_node<Q, T, CLOSURE>(h, (m & kListForced) != 0u, p);
+        if (LOCAL && WALLS) compact_local_wall<Q, T>(h, sv, p);
+        m = collide_node<Q, T, CLOSURE>(h, nd.forced, p);
+        if constexpr (REDUCE) compact_reduce_add<Q, S>(h, m, nd.forced, p, ns);
         if constexpr (PAT == kPatAB) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) St::st(B + (long long)i * nfp + t, h[i]);
+            for (int i = 0; i < Q; ++i) St::st(B + ((I)i * nfp + t), h[i]);
         } else {
             St::st(B + t, h[0]);
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const int d = sv[opp(i)];
-                St::st(B + (d >= 0 ? (long long)i * nfp + d : (long long)opp(i) * nfp + t), h[i]);
+                St::st(B + (d >= 0 ? (I)i * nfp + (I)d : (I)opp(i) * nfp + t), h[i]);
             }
         }
     }
+}
+
+template <int Q, typename S, typename I, int CLOSURE, int PAT, bool LOCAL, bool WALLS, bool REDUCE>
+__global__ void __launch_bounds__(kStepThreads)
+    k_collide_stream_compact(const S *__restrict__ A, S *__restrict__ B, CompactMap cm, I n, I nfp,
+                             KParams<typename Store<S>::T> p, float *__restrict__ partials)
+{
+    const I t = (I)blockIdx.x * (I)blockDim.x + (I)threadIdx.x;
+    NodeSums ns;
+    if (t < n) compact_node<Q, S, I, CLOSURE, PAT, LOCAL, WALLS, REDUCE>(A, B, cm, t, nfp, p, ns);
+    if constexpr (REDUCE) block_partial_f32(ns, partials + (long long)blockIdx.x * kRedSlots);
+}
+
+// The reduction over the compact copy: node t's f*_i sits at A[i][t] (AB),
+// A[opp(i)][t] (AA layout S) or, in layout P, at F[i][x + c_i], whose list
+// position is the code of direction opp(i) (F[opp(i)][t] where x + c_i is
+// a wall).  Same per-block chunking as k_reduce.
+template <int Q, typename S, int LAY, bool WALLS>
+__global__ void __launch_bounds__(kRedThreads)
+    k_reduce_compact(const S *__restrict__ A, CompactMap cm, long long n, long long nfp,
+                     KParams<typename Store<S>::T> p, double *__restrict__ partials)
+{
+    using T = typename Store<S>::T;
+    RedAcc<T> ra;
+    const long long chunk = ((n + gridDim.x - 1) / gridDim.x + 31) & ~31ll;
+    const long long lo = blockIdx.x * chunk;
+    const long long hi = lo + chunk < n ? lo + chunk : n;
+    for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+        const uint32_t entry = __ldg(cm.list + t);
+        T h[Q];
+        if constexpr (LAY == kLayP) {
+            CompactNode nd;
+            nd.init(cm, entry);
+            h[0] = Store<S>::ld(A + t);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const int d = nd.code<WALLS>(cm, opp(i));
+                h[i] = Store<S>::ld(A + (d >= 0 ? (long long)i * nfp + d : (long long)opp(i) * nfp + t));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) h[i] = Store<S>::ld(A + (long long)(LAY == kLayS ? opp(i) : i) * nfp + t);
+        }
+        T d, u[3];
+        stored_moments<Q, S>(h, (entry & kListForced) != 0u, p, d, u);
+        ra.add(d, u);
+    }
+    double acc[kRedSlots];
+    ra.slots(acc);
+    block_reduce_slots(acc);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < kRedSlots; ++k) partials[(long long)blockIdx.x * kRedSlots + k] = acc[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -898,6 +1019,10 @@ template <> struct Pair<__half> {
         const unsigned v = __ldg(reinterpret_cast<const unsigned *>(p));
         return __half22float2(*reinterpret_cast<const __half2 *>(&v));
     }
+    static __device__ __forceinline__ float2 ldc(const __half *p)
+    {
+        return __half22float2(*reinterpret_cast<const __half2 *>(p));
+    }
     static __device__ __forceinline__ void st(__half *p, float a, float b)
     {
         *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
@@ -908,6 +1033,10 @@ template <> struct Pair<__nv_bfloat16> {
     {
         const unsigned v = __ldg(reinterpret_cast<const unsigned *>(p));
         return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v));
+    }
+    static __device__ __forceinline__ float2 ldc(const __nv_bfloat16 *p)
+    {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
     }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float a, float b)
     {
@@ -921,6 +1050,11 @@ template <> struct Pair<h16s> {
         const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&v));
         return make_float2(f.x * kF16sDown, f.y * kF16sDown);
     }
+    static __device__ __forceinline__ float2 ldc(const h16s *p)
+    {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(p));
+        return make_float2(f.x * kF16sDown, f.y * kF16sDown);
+    }
     static __device__ __forceinline__ void st(h16s *p, float a, float b)
     {
         *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a * kF16sUp, b * kF16sUp);
@@ -928,6 +1062,7 @@ template <> struct Pair<h16s> {
 };
 template <> struct Pair<float> {
     static __device__ __forceinline__ float2 ld(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+    static __device__ __forceinline__ float2 ldc(const float *p) { return *reinterpret_cast<const float2 *>(p); }
     static __device__ __forceinline__ void st(float *p, float a, float b)
     {
         *reinterpret_cast<float2 *>(p) = make_float2(a, b);
@@ -1052,7 +1187,78 @@ __device__ __forceinline__ void collide_stream_pair(const S *__restrict__ A, S *
     }
 }
 
+// The even (local) AA step of two x-adjacent nodes: each reads its own
+// slots F[i][x] and writes F[opp(i)][x], so the pair moves as aligned 32-bit
+// words with no neighbour access at all; a link whose source is a moving wall
+// adds Ladd's term to the bounced value already in place.
 template <int Q, typename S, bool GENERAL, int CLOSURE, bool REDUCE>
+__device__ __forceinline__ void collide_even_pair(S *__restrict__ F, const uint8_t *__restrict__ tags, const Grid &g,
+                                                  const KParams<float> &p, int pair, int y, int z, NodeSums &ns)
+{
+    using St = Store<S>;
+    const int x0 = 2 * pair;
+    if (x0 >= g.nx) return;  // no warp-collective work in this step
+    const bool vb = x0 + 1 < g.nx;
+    const int self = (z * g.ny + y) * g.px + x0;  // even: a 4-byte aligned pair (x0 + 1 < px)
+    unsigned ta = 0, tb = 0;
+    bool act_a = true, act_b = vb;
+    if (GENERAL) {
+        const unsigned tt = __ldg(reinterpret_cast<const unsigned short *>(tags + self));
+        ta = tt & 0xffu;
+        tb = tt >> 8;
+        act_a = !is_wall_tag(ta & kTagMask);
+        act_b = vb && !is_wall_tag(tb & kTagMask);
+    }
+    if (!act_a && !act_b) return;
+    float ha[Q], hb[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float2 v = Pair<S>::ldc(F + (long long)i * g.sN + self);
+        ha[i] = v.x;
+        hb[i] = v.y;
+    }
+    bool fa = false, fb = false;
+    if (GENERAL) {
+        if (act_a && (ta & kNearWall)) {
+            Nbr nb;
+            nb.init(g, x0, y, z);
+            apply_walls<Q, S, kPatAAEven, false>(ha, F, tags, g, nb, p);
+        }
+        if (act_b && (tb & kNearWall)) {
+            Nbr nb;
+            nb.init(g, x0 + 1, y, z);
+            apply_walls<Q, S, kPatAAEven, false>(hb, F, tags, g, nb, p);
+        }
+        fa = (ta & kTagMask) == LBM_TAG_FORCED;
+        fb = (tb & kTagMask) == LBM_TAG_FORCED;
+    }
+    collide_node<Q, float, CLOSURE>(ha, fa, p);
+    collide_node<Q, float, CLOSURE>(hb, fb, p);
+    if constexpr (REDUCE) {
+        float d, u[3];
+        if (act_a) {
+            stored_moments<Q, S>(ha, fa, p, d, u);
+            ns.add(d, u);
+        }
+        if (act_b) {
+            stored_moments<Q, S>(hb, fb, p, d, u);
+            ns.add(d, u);
+        }
+    }
+    if (act_a && act_b) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Pair<S>::st(F + (long long)opp(i) * g.sN + self, ha[i], hb[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (act_a) St::st(F + (long long)opp(i) * g.sN + self, ha[i]);
+            if (act_b) St::st(F + (long long)opp(i) * g.sN + self + 1, hb[i]);
+        }
+    }
+}
+
+// PAT: kPatAB (pull from A, write B) or kPatAAEven (in place in B).
+template <int Q, typename S, bool GENERAL, int CLOSURE, bool REDUCE, int PAT>
 __device__ __forceinline__ void collide_stream_x2_body(const S *__restrict__ A, S *__restrict__ B,
                                                        const uint8_t *__restrict__ tags, const Grid &g,
                                                        const KParams<float> &p, float *__restrict__ partials)
@@ -1063,16 +1269,21 @@ __device__ __forceinline__ void collide_stream_x2_body(const S *__restrict__ A, 
     NodeSums ns;
     // y >= ny is uniform over a warp (a warp lies in one row), so skipping
     // those warps keeps every shuffle of the node work warp-complete
-    if (y < g.ny) collide_stream_pair<Q, S, GENERAL, CLOSURE, REDUCE>(A, B, tags, g, p, pair, y, z, ns);
+    if (y < g.ny) {
+        if constexpr (PAT == kPatAAEven)
+            collide_even_pair<Q, S, GENERAL, CLOSURE, REDUCE>(B, tags, g, p, pair, y, z, ns);
+        else
+            collide_stream_pair<Q, S, GENERAL, CLOSURE, REDUCE>(A, B, tags, g, p, pair, y, z, ns);
+    }
     if constexpr (REDUCE) block_partial_f32(ns, partials + linear_block() * kRedSlots);
 }
 
-template <int Q, typename S, bool GENERAL, int CLOSURE, bool REDUCE>
+template <int Q, typename S, bool GENERAL, int CLOSURE, bool REDUCE, int PAT = kPatAB>
 __global__ void __launch_bounds__(kStepThreads)
     k_collide_stream_x2(const S *__restrict__ A, S *__restrict__ B, const uint8_t *__restrict__ tags, Grid g,
                         KParams<float> p, float *__restrict__ partials)
 {
-    collide_stream_x2_body<Q, S, GENERAL, CLOSURE, REDUCE>(A, B, tags, g, p, partials);
+    collide_stream_x2_body<Q, S, GENERAL, CLOSURE, REDUCE, PAT>(A, B, tags, g, p, partials);
 }
 
 // ---------------------------------------------------------------------------
@@ -1341,6 +1552,13 @@ inline void node_launch_shape(const Grid &g, dim3 &grid, dim3 &block)
     grid = dim3((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
 }
 
+}  // namespace lbm
+
+// The TMA-fed learned-closure step (uses the node helpers above).
+#include "lbm_mlp_tma.cuh"
+
+namespace lbm {
+
 // ---------------------------------------------------------------------------
 // Launchers, defined once per storage type S by LBM_DEFINE_LAUNCHERS(S).
 // ---------------------------------------------------------------------------
@@ -1356,35 +1574,67 @@ inline void pair_launch_shape(const Grid &g, dim3 &grid, dim3 &block)
     grid = dim3((pairs + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
 }
 
-template <int Q, typename S, bool GEN, bool RED, int CLOSURE>
+template <int Q, typename S, bool GEN, bool RED, int CLOSURE, int PAT>
 void launch_x2(const Launch &L, const KParams<float> &kp, float *partials, dim3 grid, dim3 block)
 {
     const S *A = (const S *)L.A;
     S *B = (S *)L.B;
-    k_collide_stream_x2<Q, S, GEN, CLOSURE, RED><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, partials);
+    k_collide_stream_x2<Q, S, GEN, CLOSURE, RED, PAT><<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, partials);
 }
 
-template <int Q, typename S, bool GEN, bool RED>
+template <int Q, typename S, bool GEN, bool RED, int PAT>
 cudaError_t step_closure_x2(const Launch &L, const KParams<float> &kp, float *partials)
 {
     dim3 grid, block;
     pair_launch_shape(L.g, grid, block);
     switch (L.closure) {
-    case LBM_CLOSURE_BGK: launch_x2<Q, S, GEN, RED, LBM_CLOSURE_BGK>(L, kp, partials, grid, block); break;
-    case LBM_CLOSURE_SMAGORINSKY: launch_x2<Q, S, GEN, RED, LBM_CLOSURE_SMAGORINSKY>(L, kp, partials, grid, block); break;
-    case LBM_CLOSURE_TRT: launch_x2<Q, S, GEN, RED, LBM_CLOSURE_TRT>(L, kp, partials, grid, block); break;
+    case LBM_CLOSURE_BGK: launch_x2<Q, S, GEN, RED, LBM_CLOSURE_BGK, PAT>(L, kp, partials, grid, block); break;
+    case LBM_CLOSURE_SMAGORINSKY:
+        launch_x2<Q, S, GEN, RED, LBM_CLOSURE_SMAGORINSKY, PAT>(L, kp, partials, grid, block);
+        break;
+    case LBM_CLOSURE_TRT: launch_x2<Q, S, GEN, RED, LBM_CLOSURE_TRT, PAT>(L, kp, partials, grid, block); break;
     case LBM_CLOSURE_STREAM_ONLY:
         if constexpr (RED) return cudaErrorNotSupported;
-        launch_x2<Q, S, GEN, false, LBM_CLOSURE_STREAM_ONLY>(L, kp, nullptr, grid, block);
+        launch_x2<Q, S, GEN, false, LBM_CLOSURE_STREAM_ONLY, PAT>(L, kp, nullptr, grid, block);
         break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
+// The learned-closure step fed by TMA (A/B): persistent blocks, as many as
+// fit on the device at once, each walking tiles of 128 nodes of one row.
+template <int Q, typename S, bool GEN>
+cudaError_t step_mlp_tma(const Launch &L, const KParams<typename Store<S>::T> &kp)
+{
+    static int wave = 0;  // resident blocks of this instantiation, found on first use
+    constexpr size_t dyn = tma_smem_bytes<Q, S>();
+    if (wave == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_collide_stream_mlp_tma<Q, S, GEN>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, occ = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_collide_stream_mlp_tma<Q, S, GEN>,
+                                                               kTmaThreads, dyn)) != cudaSuccess)
+            return e;
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+        wave = sms * occ;
+    }
+    const int ntx = (L.g.nx + kTileM - 1) / kTileM;
+    const long long ntiles = (long long)ntx * L.g.ny * L.g.nz;
+    const unsigned blocks = (unsigned)(ntiles < wave ? ntiles : wave);
+    k_collide_stream_mlp_tma<Q, S, GEN><<<blocks, kTmaThreads, dyn, L.stream>>>(
+        *L.tma_A, (const S *)L.A, (S *)L.B, L.tags, L.g, kp, (const MlpSmem *)L.mlp_image, ntx, ntiles);
+    return cudaGetLastError();
+}
+
 // One dense step launch.  RED: fused step-and-reduce (FP32 compute; BGK,
 // Smagorinsky and TRT).  PAT: streaming pattern (the two-nodes-per-thread
-// 16-bit kernel is A/B only; AA steps take one node per thread).
+// 16-bit kernel serves A/B steps and the local even AA steps; the odd AA
+// steps, which read and write the neighbours' slots, take one node per
+// thread).
 template <int Q, typename S, bool GEN, bool RED, int PAT>
 cudaError_t step_closure(const Launch &L, const KParams<typename Store<S>::T> &kp, dim3 grid, dim3 block,
                          float *partials)
@@ -1397,12 +1647,14 @@ cudaError_t step_closure(const Launch &L, const KParams<typename Store<S>::T> &k
         if (L.closure == LBM_CLOSURE_MLP) {
             if (RED) return cudaErrorNotSupported;
             if (!L.mlp_image) return cudaErrorInvalidValue;
+            if constexpr (PAT == kPatAB)
+                if (L.tma_A) return step_mlp_tma<Q, S, GEN>(L, kp);
             k_collide_stream_mlp<Q, S, GEN, PAT>
                 <<<grid, block, 0, L.stream>>>(A, B, L.tags, L.g, kp, (const MlpSmem *)L.mlp_image);
             return cudaGetLastError();
         }
-        if constexpr (use_pairs<S>() && PAT == kPatAB) {
-            if (L.g.px >= 64 && !kp.wall_local) return step_closure_x2<Q, S, GEN, RED>(L, kp, partials);
+        if constexpr (use_pairs<S>() && (PAT == kPatAB || PAT == kPatAAEven)) {
+            if (L.g.px >= 64 && !kp.wall_local) return step_closure_x2<Q, S, GEN, RED, PAT>(L, kp, partials);
         }
         switch (L.closure) {
         case LBM_CLOSURE_BGK:
@@ -1432,7 +1684,7 @@ cudaError_t step_closure(const Launch &L, const KParams<typename Store<S>::T> &k
 inline long long fused_partials(const Launch &L, const lbm_params &p, size_t elem)
 {
     dim3 grid, block;
-    if (elem == 2 && !L.aa && L.g.px >= 64 && !p.wall_rho_local)
+    if (elem == 2 && (!L.aa || L.aa_p) && L.g.px >= 64 && !p.wall_rho_local)
         pair_launch_shape(L.g, grid, block);
     else
         node_launch_shape(L.g, grid, block);
@@ -1457,43 +1709,76 @@ template <int Q, typename S, int PAT> cudaError_t step_reduce_q(const Launch &L,
                      : step_closure<Q, S, false, true, PAT>(L, kp, grid, block, partials);
 }
 
-template <int Q, typename S, int PAT, bool LOCAL>
-cudaError_t step_compact_local(const Launch &L, const KParams<typename Store<S>::T> &kp, const void *Ac, void *Bc,
-                               const int *nbr, long long nfp)
+template <int Q, typename S, int CLOSURE, int PAT, bool LOCAL, bool WALLS, bool RED>
+cudaError_t compact_launch(const Launch &L, const KParams<typename Store<S>::T> &kp, const void *Ac, void *Bc,
+                           long long nfp, float *partials)
 {
     const unsigned blocks = (unsigned)((L.n_list + kStepThreads - 1) / kStepThreads);
     if (blocks == 0) return cudaSuccess;
     const S *A = (const S *)Ac;
     S *B = (S *)Bc;
-    switch (L.closure) {
-    case LBM_CLOSURE_BGK:
-        k_collide_stream_compact<Q, S, LBM_CLOSURE_BGK, PAT, LOCAL>
-            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
-        break;
-    case LBM_CLOSURE_SMAGORINSKY:
-        k_collide_stream_compact<Q, S, LBM_CLOSURE_SMAGORINSKY, PAT, LOCAL>
-            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
-        break;
-    case LBM_CLOSURE_STREAM_ONLY:
-        k_collide_stream_compact<Q, S, LBM_CLOSURE_STREAM_ONLY, PAT, LOCAL>
-            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
-        break;
-    case LBM_CLOSURE_TRT:
-        k_collide_stream_compact<Q, S, LBM_CLOSURE_TRT, PAT, LOCAL>
-            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, nbr, L.fluid_mask, L.n_list, nfp, kp);
-        break;
-    default: return cudaErrorInvalidValue;
-    }
+    if ((long long)Q * nfp <= 0xffffffffll)  // 32-bit element indices
+        k_collide_stream_compact<Q, S, uint32_t, CLOSURE, PAT, LOCAL, WALLS, RED><<<blocks, kStepThreads, 0, L.stream>>>(
+            A, B, L.cmap, (uint32_t)L.n_list, (uint32_t)nfp, kp, partials);
+    else
+        k_collide_stream_compact<Q, S, long long, CLOSURE, PAT, LOCAL, WALLS, RED>
+            <<<blocks, kStepThreads, 0, L.stream>>>(A, B, L.cmap, L.n_list, nfp, kp, partials);
     return cudaGetLastError();
 }
 
+template <int Q, typename S, int PAT, bool LOCAL, bool WALLS, bool RED>
+cudaError_t step_compact_closure(const Launch &L, const KParams<typename Store<S>::T> &kp, const void *Ac, void *Bc,
+                                 long long nfp, float *partials)
+{
+    if constexpr (RED && sizeof(typename Store<S>::T) != 4) {
+        return cudaErrorNotSupported;
+    } else {
+        switch (L.closure) {
+        case LBM_CLOSURE_BGK:
+            return compact_launch<Q, S, LBM_CLOSURE_BGK, PAT, LOCAL, WALLS, RED>(L, kp, Ac, Bc, nfp, partials);
+        case LBM_CLOSURE_SMAGORINSKY:
+            return compact_launch<Q, S, LBM_CLOSURE_SMAGORINSKY, PAT, LOCAL, WALLS, RED>(L, kp, Ac, Bc, nfp, partials);
+        case LBM_CLOSURE_TRT:
+            return compact_launch<Q, S, LBM_CLOSURE_TRT, PAT, LOCAL, WALLS, RED>(L, kp, Ac, Bc, nfp, partials);
+        case LBM_CLOSURE_STREAM_ONLY:
+            if constexpr (RED) return cudaErrorNotSupported;
+            return compact_launch<Q, S, LBM_CLOSURE_STREAM_ONLY, PAT, LOCAL, WALLS, false>(L, kp, Ac, Bc, nfp,
+                                                                                          nullptr);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+}
+
+// The local-density wall only matters next to moving walls.
 template <int Q, typename S, int PAT>
-cudaError_t step_compact_q(const Launch &L, const lbm_params &p, const void *Ac, void *Bc, const int *nbr,
-                           long long nfp)
+cudaError_t step_compact_q(const Launch &L, const lbm_params &p, const void *Ac, void *Bc, long long nfp,
+                           float *partials)
 {
     const auto kp = make_kparams<typename Store<S>::T>(Q, p);
-    return kp.wall_local ? step_compact_local<Q, S, PAT, true>(L, kp, Ac, Bc, nbr, nfp)
-                         : step_compact_local<Q, S, PAT, false>(L, kp, Ac, Bc, nbr, nfp);
+    if (!L.moving_walls)
+        return partials ? step_compact_closure<Q, S, PAT, false, false, true>(L, kp, Ac, Bc, nfp, partials)
+                        : step_compact_closure<Q, S, PAT, false, false, false>(L, kp, Ac, Bc, nfp, nullptr);
+    if (kp.wall_local)
+        return partials ? step_compact_closure<Q, S, PAT, true, true, true>(L, kp, Ac, Bc, nfp, partials)
+                        : step_compact_closure<Q, S, PAT, true, true, false>(L, kp, Ac, Bc, nfp, nullptr);
+    return partials ? step_compact_closure<Q, S, PAT, false, true, true>(L, kp, Ac, Bc, nfp, partials)
+                    : step_compact_closure<Q, S, PAT, false, true, false>(L, kp, Ac, Bc, nfp, nullptr);
+}
+
+template <int Q, typename S, int LAY>
+cudaError_t reduce_compact_q(const Launch &L, const lbm_params &p, const void *Ac, long long nfp, double *partials,
+                             int nblocks, double *out)
+{
+    const auto kp = make_kparams<typename Store<S>::T>(Q, p);
+    const S *A = (const S *)Ac;
+    if (L.moving_walls)
+        k_reduce_compact<Q, S, LAY, true><<<nblocks, kRedThreads, 0, L.stream>>>(A, L.cmap, L.n_list, nfp, kp, partials);
+    else
+        k_reduce_compact<Q, S, LAY, false><<<nblocks, kRedThreads, 0, L.stream>>>(A, L.cmap, L.n_list, nfp, kp, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_final<<<1, kRedThreads, 0, L.stream>>>(partials, nblocks, out);
+    return cudaGetLastError();
 }
 
 // Blocks of `threads` threads of `kernel` that fit on the device at once.
@@ -1578,13 +1863,23 @@ template <int Q, typename S, int LAY> cudaError_t get_pop_q(const Launch &L, int
     }                                                                                                        \
     template <>                                                                                              \
     cudaError_t launch_step_compact_aa<S>(const Launch &L, const lbm_params &p, const void *Ac, void *Bc,    \
-                                          const int *nbr, long long nfp)                                     \
+                                          long long nfp, float *partials)                                    \
     {                                                                                                        \
         if (L.aa_p)                                                                                          \
-            return L.Q == 19 ? step_compact_q<19, S, kPatAAEven>(L, p, Ac, Bc, nbr, nfp)                     \
-                             : step_compact_q<27, S, kPatAAEven>(L, p, Ac, Bc, nbr, nfp);                    \
-        return L.Q == 19 ? step_compact_q<19, S, kPatAAOdd>(L, p, Ac, Bc, nbr, nfp)                          \
-                         : step_compact_q<27, S, kPatAAOdd>(L, p, Ac, Bc, nbr, nfp);                         \
+            return L.Q == 19 ? step_compact_q<19, S, kPatAAEven>(L, p, Ac, Bc, nfp, partials)                \
+                             : step_compact_q<27, S, kPatAAEven>(L, p, Ac, Bc, nfp, partials);               \
+        return L.Q == 19 ? step_compact_q<19, S, kPatAAOdd>(L, p, Ac, Bc, nfp, partials)                     \
+                         : step_compact_q<27, S, kPatAAOdd>(L, p, Ac, Bc, nfp, partials);                    \
+    }                                                                                                        \
+    template <>                                                                                              \
+    cudaError_t launch_reduce_compact_aa<S>(const Launch &L, const lbm_params &p, const void *Ac, long long nfp, \
+                                            double *partials, int nb, double *out)                           \
+    {                                                                                                        \
+        if (L.aa_p)                                                                                          \
+            return L.Q == 19 ? reduce_compact_q<19, S, kLayP>(L, p, Ac, nfp, partials, nb, out)              \
+                             : reduce_compact_q<27, S, kLayP>(L, p, Ac, nfp, partials, nb, out);             \
+        return L.Q == 19 ? reduce_compact_q<19, S, kLayS>(L, p, Ac, nfp, partials, nb, out)                  \
+                         : reduce_compact_q<27, S, kLayS>(L, p, Ac, nfp, partials, nb, out);                 \
     }                                                                                                        \
     template <>                                                                                              \
     cudaError_t launch_reduce_aa<S>(const Launch &L, const lbm_params &p, double *partials, int nb, double *out) \
@@ -1621,11 +1916,19 @@ template <int Q, typename S, int LAY> cudaError_t get_pop_q(const Launch &L, int
     }                                                                                                        \
     template <>                                                                                              \
     cudaError_t launch_step_compact<S>(const Launch &L, const lbm_params &p, const void *Ac, void *Bc,       \
-                                       const int *nbr, long long nfp)                                        \
+                                       long long nfp, float *partials)                                       \
     {                                                                                                        \
-        if (L.aa) return launch_step_compact_aa<S>(L, p, Ac, Bc, nbr, nfp);                                  \
-        return L.Q == 19 ? step_compact_q<19, S, kPatAB>(L, p, Ac, Bc, nbr, nfp)                             \
-                         : step_compact_q<27, S, kPatAB>(L, p, Ac, Bc, nbr, nfp);                            \
+        if (L.aa) return launch_step_compact_aa<S>(L, p, Ac, Bc, nfp, partials);                             \
+        return L.Q == 19 ? step_compact_q<19, S, kPatAB>(L, p, Ac, Bc, nfp, partials)                        \
+                         : step_compact_q<27, S, kPatAB>(L, p, Ac, Bc, nfp, partials);                       \
+    }                                                                                                        \
+    template <>                                                                                              \
+    cudaError_t launch_reduce_compact<S>(const Launch &L, const lbm_params &p, const void *Ac, long long nfp, \
+                                         double *partials, int nb, double *out)                              \
+    {                                                                                                        \
+        if (L.aa) return launch_reduce_compact_aa<S>(L, p, Ac, nfp, partials, nb, out);                      \
+        return L.Q == 19 ? reduce_compact_q<19, S, kLayAB>(L, p, Ac, nfp, partials, nb, out)                 \
+                         : reduce_compact_q<27, S, kLayAB>(L, p, Ac, nfp, partials, nb, out);                \
     }                                                                                                        \
     template <> cudaError_t launch_step<S>(const Launch &L, const lbm_params &p)                             \
     {                                                                                                        \

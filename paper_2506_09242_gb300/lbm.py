@@ -108,6 +108,7 @@ SIGNATURES = {
     "lbm_get_state": (_I, [_P, _P, _SZ, ctypes.POINTER(_I), ctypes.POINTER(_LL), _I]),
     "lbm_set_state": (_I, [_P, _P, _SZ, _I, _LL, _I]),
     "lbm_info": (_I, [_P, ctypes.POINTER(_SZ), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "lbm_fp64_fma_rate": (_I, [_P, ctypes.POINTER(ctypes.c_double)]),
     "lbm_last_error": (ctypes.c_char_p, [_P]),
     "lbm_geometry_spheres": (_I, [_P, _P, _P, _I, _D, ctypes.c_uint8, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "lbm_enstrophy": (_I, [_P, ctypes.POINTER(_D)]),
@@ -508,6 +509,19 @@ def reduce_noalloc(h, Q: int, dtype, nx: int, ny: int, nz: int, tags=None, force
         raise UnstableError(st, lib.lbm_last_error(None).decode(), out.as_dict())
     _check(st, None)
     return out.as_dict()
+
+
+def fp64_fma_rate(stream=None) -> float:
+    """FP64 operations per second of the current device (an FMA counts as
+    two), measured by the library's FMA-chain kernel on torch's current
+    stream: the arithmetic roof of the step on FP64 storage."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    out = ctypes.c_double()
+    _check(load().lbm_fp64_fma_rate(handle, ctypes.byref(out)), None)
+    return out.value
 
 
 # -- closure training calls (device tensors, torch's current stream) ---------

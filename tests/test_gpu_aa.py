@@ -5,12 +5,11 @@ The AA steps run the same per-node arithmetic as the A/B steps and differ
 only in where each population is read and written, so whenever both patterns
 use the same node kernel the results must be bit-identical: populations,
 moments and reductions, after odd step counts (the neighbour-shifted layout)
-and even ones, through graph replays and fused step-and-reduce calls.  Two
-exceptions compare to rounding instead: 16-bit storage on rows of 64 nodes or
-more (A/B takes the two-nodes-per-thread kernel, whose FP32 rounding can
-differ from the one-node kernel by one storage ulp), and the compact
-fluid-only storage (its A/B step relaxes one direction at a time, its AA
-steps pair opposite directions: the same algebra, rounded differently).
+and even ones, through graph replays and fused step-and-reduce calls, on
+dense and on compact fluid-only storage.  One exception compares to rounding
+instead: 16-bit storage on rows of 64 nodes or more (A/B takes the
+two-nodes-per-thread kernel, whose FP32 rounding can differ from the
+one-node kernel by one storage ulp).
 """
 import numpy as np
 import pytest
@@ -102,10 +101,7 @@ def test_aa_is_bit_identical_to_ab(dtype, mix, closure):
     params = dict(tau=0.63, force=(1e-4, -5e-5, 2e-5), wall_u=WALLS, closure=closure)
     ab, aa = run_both(shape, 19, dtype, tags, params, (1, 1, 7, 8, 3), rho, u)
     for a, b in zip(ab, aa):
-        if mix == "list":  # compact storage: the two patterns round differently
-            assert_close(a, b, 1e-12 if dtype == "f64" else 2e-5)
-        else:
-            assert_same(a, b)
+        assert_same(a, b)
 
 
 @pytest.mark.parametrize("Q", [19, 27])
@@ -117,12 +113,8 @@ def test_aa_d3q27_and_degenerate_rows(Q):
         tags.flat[0] = oracle.FORCED
         params = dict(tau=0.8, force=(1e-3, 0.0, -1e-3), wall_u=WALLS)
         ab, aa = run_both(shape, Q, "f64", tags, params, (1, 2, 5))
-        walls = np.mean(tags >= oracle.SOLID)
         for a, b in zip(ab, aa):
-            if walls > 0.3:  # compact storage: the patterns round differently
-                assert_close(a, b, 1e-12)
-            else:
-                assert_same(a, b)
+            assert_same(a, b)
 
 
 @pytest.mark.parametrize("kind", ["f16", "bf16", "f16s"])
@@ -169,12 +161,14 @@ def test_aa_matches_the_oracle():
     lat.close()
 
 
+@pytest.mark.parametrize("mix", ["dense", "list"])
 @pytest.mark.parametrize("dtype", ["f32", "f16"])
-def test_aa_fused_step_reduce(dtype):
+def test_aa_fused_step_reduce(dtype, mix):
     """The fused last step writes the same state and, with the one-node
-    kernel on both sides, the same partial sums."""
+    kernel on both sides (or the compact kernel, for "list" tags), the same
+    partial sums."""
     shape = (7, 9, 30)  # rows padded to 32: the one-node kernel in both patterns
-    tags = inp.random_tags(shape, seed=78, n_walls=2, **WALL_MIX["dense"])
+    tags = inp.random_tags(shape, seed=78, n_walls=2, **WALL_MIX[mix])
     rho, u = inp.random_velocity_field(shape, seed=79, amplitude=0.04)
     params = dict(tau=0.66, force=(1e-4, 0, 0), wall_u=WALLS)
     ab, aa = run_both(shape, 19, dtype, tags, params, (1, 6, 3), rho, u, fused=True)
