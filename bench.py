@@ -355,6 +355,8 @@ CPU_PLANS = {
     # the full measurement plan: single thread and all cores, 128^3 and 256^3,
     # D3Q19 and D3Q27, 10 steps after 2 warm-up steps, 3 repeats
     "full": [(q, n, t, 2, 10, 3) for t in (0, 1) for n in (128, 256) for q in (19, 27)],
+    # its single-thread half (one core; can run beside other work)
+    "single": [(q, n, 1, 2, 10, 3) for n in (128, 256) for q in (19, 27)],
 }
 
 

@@ -8,8 +8,9 @@ Every numerical step runs in the CUDA library through the C ABI:
 - the closure inside the collide kernel;
 - the FP64 reductions.
 
-Python only sequences the calls. torch holds device buffers, draws minibatch
-indices and takes means of small filtered fields.
+Python sequences the calls. torch holds device buffers, draws minibatch
+indices and takes one mean outside the library: the kinetic energy of the
+box-filtered velocity, 0.5 <|u_filtered|^2>, over the coarse grid's cells.
 
 Workflow (no counterpart in the paper; the TGV set-up is Sec. 3.1's):
 1. Fine runs at resolution n_f and Reynolds numbers Re (u0 = 0.04,
@@ -112,8 +113,8 @@ def fine_run(n: int, re: float, factor: int, *, t_end: float = 10.0, k_every: fl
             break
         ub = lbm.box_filter(u_d, factor)
         times.append(j * k_every)
-        ks.append(0.5 * float((ub * ub).sum(dim=0).mean()))
-        kf.append(0.5 * float((u_d * u_d).sum(dim=0).mean()))
+        ks.append(0.5 * float((ub * ub).sum(dim=0).mean()))  # the filtered field's mean energy (torch)
+        kf.append(lat.reduce()["ke"] / n ** 3)  # the library's FP64 reduction (every node is fluid)
         if j % every == 0 and j > 0:
             X, y = lbm.coarse_samples(rho_d, u_d, factor, tau_c)
             idx = torch.randint(0, X.shape[0], (min(samples_per_snapshot, X.shape[0]),), generator=gen,
