@@ -1568,7 +1568,9 @@ template <typename S> constexpr bool use_pairs() { return sizeof(S) == 2; }
 inline void pair_launch_shape(const Grid &g, dim3 &grid, dim3 &block)
 {
     const int pairs = g.px / 2;                  // px is a multiple of 32
-    const int bx = pairs >= 64 ? 64 : 32;        // whole warps along x
+    // whole warps along x; 64 pairs per block row only where rows hold a
+    // multiple of 64 pairs (otherwise the last block of a row idles)
+    const int bx = pairs % 64 == 0 ? 64 : 32;
     const int by = kStepThreads / bx;
     block = dim3(bx, by, 1);
     grid = dim3((pairs + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
