@@ -684,3 +684,31 @@ def test_full_size_cavity256_f32_sampled():
     d = _sampled_check(lat, 19, "f32", None, None, tags, params, cells)
     assert d <= 1e-7
     lat.close()
+
+
+@pytest.mark.parametrize("pattern,closure", [("ab", "trt"), ("aa", "bgk")])
+def test_full_size_porous400_f32_sampled(pattern, closure):
+    """The porous benchmark workload at its full size (400^3 random-sphere
+    medium, 80% wall: stepped on compact fluid-only storage): one step from a
+    random equilibrium, sampled pore nodes (among them nodes with solid
+    neighbours) against the oracle's step of their 3x3x3 neighbourhood."""
+    n = 400
+    centres, radii = inp.sphere_list((n, n, n), seed=2506, rmin=4.0, rmax=10.0, count=100_000)
+    lat = lbm.Lattice(n, n, n, 19, "f32", pattern=pattern)
+    lat.geometry_spheres(centres, radii, 0.2, lbm.TAG_FORCED)
+    kind = {"bgk": (lbm.CLOSURE_BGK, oracle.BGK), "trt": (lbm.CLOSURE_TRT, oracle.TRT)}[closure]
+    lat.set_params(1.0, force=(1e-6, 0.0, 0.0), closure=kind[0])
+    tags = lat.get_tags()
+    rho, u = inp.random_velocity_field((n, n, n), seed=41, amplitude=0.05)
+    lat.init_equilibrium(rho, u)
+    lat.step(1)
+    rng = np.random.default_rng(2)
+    pore = np.argwhere(tags < oracle.SOLID)
+    cells = pore[rng.choice(len(pore), 48, replace=False)]
+    near = [c for c in pore[rng.choice(len(pore), 4000, replace=False)]
+            if np.any(_neighbourhood(tags, *c) >= oracle.SOLID)][:16]
+    assert len(near) == 16
+    cells = np.vstack([cells, np.array(near)])
+    d = _sampled_check(lat, 19, "f32", rho, u, tags, dict(tau=1.0, force=(1e-6, 0.0, 0.0), closure=kind[1]), cells)
+    assert d <= 1e-7
+    lat.close()
