@@ -191,7 +191,11 @@ lbm_status lbm_tag_census(lbm_ctx *ctx, long long *counts);
 /* Equilibrium initial state (Sec. 3.1, used for the Taylor-Green vortex):
  * f*_i = f_eq_i(rho, u) on every node, written to both population arrays.
  * rho: N values or NULL (uniform 1); u: [3][N] or NULL (rest).  Resets the
- * step counter.  Asynchronous for device inputs.  Errors: CUDA, OOM. */
+ * step counter.  Asynchronous for device inputs.  Host inputs that are
+ * page-locked (cudaHostAlloc, cudaHostRegister, torch's pin_memory) are read
+ * by the initialisation kernel directly over the host-device link; other
+ * host inputs go through a device staging buffer.  Either way the call
+ * returns once the host buffers are no longer needed.  Errors: CUDA, OOM. */
 lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u, int on_device);
 
 /* Advances n >= 0 steps of fused pull collide-and-stream (Sec. 2.3.1):

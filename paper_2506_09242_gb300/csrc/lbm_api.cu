@@ -662,13 +662,39 @@ lbm_status lbm_tag_census(lbm_ctx *ctx, long long *counts)
     return LBM_OK;
 }
 
+// The device address of page-locked host memory that the device can read
+// directly (pinned by cudaHostAlloc or cudaHostRegister, mapped into the
+// device's address space), or NULL for any other pointer.
+static const void *device_view_of_pinned(const void *p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u, int on_device)
 {
     if (!ctx) return fail(ctx, LBM_ERR_ARG, "NULL context");
     const size_t nb = sizeof(double) * (size_t)ctx->g.N;
     Launch L = make_launch(ctx);
     lbm_status s = LBM_OK;
-    if (on_device || (!rho && !u)) {
+    const double *rho_view = on_device ? nullptr : (const double *)device_view_of_pinned(rho);
+    const double *u_view = on_device ? nullptr : (const double *)device_view_of_pinned(u);
+    if (!on_device && (rho || u) && (!rho || rho_view) && (!u || u_view)) {
+        // Page-locked host fields: the kernel reads them over the host link
+        // directly (one pass, no staging buffer, no copy-engine transfer);
+        // they must stay valid until the kernel ends, hence the wait.
+        CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
+                     using S = std::remove_pointer_t<decltype(tag)>;
+                     return launch_init<S>(L, rho_view, u_view);
+                 }),
+                 "init");
+        s = sync(ctx);
+    } else if (on_device || (!rho && !u)) {
         CUDA_TRY(ctx, by_dtype(ctx->dtype, [&](auto *tag) {
                      using S = std::remove_pointer_t<decltype(tag)>;
                      return launch_init<S>(L, rho, u);
