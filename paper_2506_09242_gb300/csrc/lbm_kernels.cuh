@@ -216,6 +216,12 @@ template <typename T> struct RedAcc {
     }
 };
 
+// Additions and multiplications rounded once each, never contracted.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // Density deviation and velocity of one node from its post-collision set as
 // it is stored (rounded to the storage type), the same quantities
 // node_moments reads back from memory.
@@ -224,27 +230,29 @@ __device__ __forceinline__ void stored_moments(const typename Store<S>::T (&h)[Q
                                                const KParams<typename Store<S>::T> &p, typename Store<S>::T &drho,
                                                typename Store<S>::T (&u)[3])
 {
+    // Roundings spelled out as in NodeSums::add.
     using T = typename Store<S>::T;
     T d = T(0), jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const T v = Store<S>::rt(h[i]);
-        d += v;
-        if (cvel(i, 0)) jx += cvel(i, 0) > 0 ? v : -v;
-        if (cvel(i, 1)) jy += cvel(i, 1) > 0 ? v : -v;
-        if (cvel(i, 2)) jz += cvel(i, 2) > 0 ? v : -v;
+        d = add_rn(d, v);
+        if (cvel(i, 0)) jx = add_rn(jx, cvel(i, 0) > 0 ? v : -v);
+        if (cvel(i, 1)) jy = add_rn(jy, cvel(i, 1) > 0 ? v : -v);
+        if (cvel(i, 2)) jz = add_rn(jz, cvel(i, 2) > 0 ? v : -v);
     }
-    const T rho = T(1) + d;
+    const T rho = add_rn(T(1), d);
     if (forced) {
-        jx -= T(0.5) * rho * p.force[0];
-        jy -= T(0.5) * rho * p.force[1];
-        jz -= T(0.5) * rho * p.force[2];
+        const T hr = mul_rn(T(-0.5), rho);
+        jx = fma(hr, p.force[0], jx);
+        jy = fma(hr, p.force[1], jy);
+        jz = fma(hr, p.force[2], jz);
     }
     const T inv = T(1) / rho;
     drho = d;
-    u[0] = jx * inv;
-    u[1] = jy * inv;
-    u[2] = jz * inv;
+    u[0] = mul_rn(jx, inv);
+    u[1] = mul_rn(jy, inv);
+    u[2] = mul_rn(jz, inv);
 }
 
 // Reduction slots of the nodes one thread owns inside a fused step, in FP32.
@@ -256,23 +264,26 @@ struct NodeSums {
     float s[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dmass, mom[3], vel[3], ke, ke_rho
     float usq_max = 0.f;
     unsigned n_fluid = 0, n_bad = 0;
+    // Every rounding is spelled out (fused multiply-adds and _rn operations,
+    // which the compiler never contracts or splits), so that each kernel
+    // that inlines this sums a node with the same bits.
     __device__ __forceinline__ void add(float d, const float (&u)[3])
     {
-        const float rho = 1.f + d;
-        const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const float rho = __fadd_rn(1.f, d);
+        const float usq = fmaf(u[2], u[2], fmaf(u[1], u[1], __fmul_rn(u[0], u[0])));
         ++n_fluid;
         if (!isfinite(rho) || !isfinite(usq)) {
             ++n_bad;
             return;
         }
-        s[0] += d;
+        s[0] = __fadd_rn(s[0], d);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            s[1 + k] += rho * u[k];
-            s[4 + k] += u[k];
+            s[1 + k] = fmaf(rho, u[k], s[1 + k]);
+            s[4 + k] = __fadd_rn(s[4 + k], u[k]);
         }
-        s[7] += 0.5f * usq;
-        s[8] += 0.5f * rho * usq;
+        s[7] = fmaf(0.5f, usq, s[7]);
+        s[8] = fmaf(__fmul_rn(0.5f, rho), usq, s[8]);
         usq_max = fmaxf(usq_max, usq);
     }
 };
@@ -1245,14 +1256,19 @@ __device__ __forceinline__ void collide_even_pair(S *__restrict__ F, const uint8
             ns.add(d, u);
         }
     }
+    // The store addresses are those of the loads; taking them again from an
+    // offset the compiler cannot see through keeps it from holding all Q of
+    // them live across the collisions.
+    int so = self;
+    asm volatile("" : "+r"(so));
     if (act_a && act_b) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) Pair<S>::st(F + (long long)opp(i) * g.sN + self, ha[i], hb[i]);
+        for (int i = 0; i < Q; ++i) Pair<S>::st(F + (long long)opp(i) * g.sN + so, ha[i], hb[i]);
     } else {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            if (act_a) St::st(F + (long long)opp(i) * g.sN + self, ha[i]);
-            if (act_b) St::st(F + (long long)opp(i) * g.sN + self + 1, hb[i]);
+            if (act_a) St::st(F + (long long)opp(i) * g.sN + so, ha[i]);
+            if (act_b) St::st(F + (long long)opp(i) * g.sN + so + 1, hb[i]);
         }
     }
 }
