@@ -425,7 +425,7 @@ __device__ __forceinline__ uint32_t apply_walls(typename Store<S>::T (&h)[Q], co
         for (int i = 1; i < Q; ++i)
             if ((wall >> i) & 1u) {
                 const unsigned ts = tags[nb.src(i)] & kTagMask;
-                if (ts >= LBM_TAG_WALL0) h[i] += rw * wall_term<Q, T>(i, ts, p);
+                if (ts >= LBM_TAG_WALL0) h[i] = fma(rw, wall_term<Q, T>(i, ts, p), h[i]);
             }
     }
     return wall;
@@ -472,17 +472,17 @@ __device__ __forceinline__ Macro<T> node_macros(const T (&h)[Q], bool forced, co
     m.rho = T(1) + drho;
     m.Gx = m.Gy = m.Gz = T(0);
     if (forced) {
-        m.Gx = m.rho * p.force[0];
-        m.Gy = m.rho * p.force[1];
-        m.Gz = m.rho * p.force[2];
-        jx += T(0.5) * m.Gx;
-        jy += T(0.5) * m.Gy;
-        jz += T(0.5) * m.Gz;
+        m.Gx = mul_rn(m.rho, p.force[0]);
+        m.Gy = mul_rn(m.rho, p.force[1]);
+        m.Gz = mul_rn(m.rho, p.force[2]);
+        jx = fma(T(0.5), m.Gx, jx);
+        jy = fma(T(0.5), m.Gy, jy);
+        jz = fma(T(0.5), m.Gz, jz);
     }
     m.inv = T(1) / m.rho;
-    m.ux = jx * m.inv;
-    m.uy = jy * m.inv;
-    m.uz = jz * m.inv;
+    m.ux = mul_rn(jx, m.inv);
+    m.uy = mul_rn(jy, m.inv);
+    m.uz = mul_rn(jz, m.inv);
     return m;
 }
 
@@ -505,13 +505,14 @@ __device__ __forceinline__ void pi_neq(const T (&h)[Q], const Macro<T> &m, T (&p
         if (cx * cz) { const T v = cx * cz > 0 ? h[i] : -h[i]; sxz = fxz ? v : sxz + v; fxz = false; }
         if (cy * cz) { const T v = cy * cz > 0 ? h[i] : -h[i]; syz = fyz ? v : syz + v; fyz = false; }
     }
-    const T d3 = m.drho * (T(1) / T(3));
-    pi[0] = sxx - m.rho * m.ux * m.ux - d3;
-    pi[1] = syy - m.rho * m.uy * m.uy - d3;
-    pi[2] = szz - m.rho * m.uz * m.uz - d3;
-    pi[3] = sxy - m.rho * m.ux * m.uy;
-    pi[4] = sxz - m.rho * m.ux * m.uz;
-    pi[5] = syz - m.rho * m.uy * m.uz;
+    const T third = T(1) / T(3);
+    const T rx = mul_rn(m.rho, m.ux), ry = mul_rn(m.rho, m.uy);
+    pi[0] = fma(-m.drho, third, fma(-rx, m.ux, sxx));
+    pi[1] = fma(-m.drho, third, fma(-ry, m.uy, syy));
+    pi[2] = fma(-m.drho, third, fma(-mul_rn(m.rho, m.uz), m.uz, szz));
+    pi[3] = fma(-rx, m.uy, sxy);
+    pi[4] = fma(-rx, m.uz, sxz);
+    pi[5] = fma(-ry, m.uz, syz);
 }
 
 // h_i <- h_i + omega (h_eq_i - h_i) + (1 - omega / 2) F_i, the rest
@@ -522,50 +523,30 @@ __device__ __forceinline__ void pi_neq(const T (&h)[Q], const Macro<T> &m, T (&p
 template <int Q, typename T>
 __device__ __forceinline__ void relax(T (&h)[Q], const Macro<T> &m, T omega, bool forced)
 {
-    const T usq15 = T(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
-    const T cf = T(1) - T(0.5) * omega;
-    const T uG = m.ux * m.Gx + m.uy * m.Gy + m.uz * m.Gz;
+    const T usq15 = mul_rn(T(1.5), fma(m.uz, m.uz, fma(m.uy, m.uy, mul_rn(m.ux, m.ux))));
+    const T cf = fma(T(-0.5), omega, T(1));
+    const T uG = fma(m.uz, m.Gz, fma(m.uy, m.Gy, mul_rn(m.ux, m.Gx)));
     {
         const T w0 = wgt<T>(Q, 0);
-        T h0 = h[0] + omega * (w0 * (m.drho - m.rho * usq15) - h[0]);
-        if (forced) h0 += cf * (w0 * (T(-3) * uG));
+        T h0 = fma(omega, fma(w0, fma(-m.rho, usq15, m.drho), -h[0]), h[0]);
+        if (forced) h0 = fma(cf, mul_rn(w0, mul_rn(T(-3), uG)), h0);
         h[0] = h0;
     }
-    if constexpr (Q == 27 && sizeof(T) == 4) {
-        // One direction at a time with the full dot products: the same
-        // algebra as the paired form below.  For D3Q27 in FP32 the 16-bit
-        // two-node kernel compiles this form to 80 registers (the paired form
-        // to 86-90), which keeps six blocks per SM resident instead of five.
-        // FP64 compute, bound by the FP64 rate, takes the paired form.
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const int cx = cvel(i, 0), cy = cvel(i, 1), cz = cvel(i, 2);
-            const T cu = T(cx) * m.ux + T(cy) * m.uy + T(cz) * m.uz;
-            const T w = wgt<T>(Q, i);
-            const T heq = w * (m.drho + m.rho * (cu * (T(3) + T(4.5) * cu) - usq15));
-            T hn = h[i] + omega * (heq - h[i]);
-            if (forced) {
-                const T cG = T(cx) * m.Gx + T(cy) * m.Gy + T(cz) * m.Gz;
-                hn += cf * w * (T(3) * (cG - uG) + T(9) * cu * cG);
-            }
-            h[i] = hn;
-        }
-        return;
-    }
-    const T r3 = T(3) * m.rho;
+    const T r3 = mul_rn(T(3), m.rho);
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
         const T cu = cdot<T>(i, m.ux, m.uy, m.uz);
         const T w = wgt<T>(Q, i);
-        const T S = w * (m.drho + m.rho * (T(4.5) * cu * cu - usq15));
-        const T A = (w * r3) * cu;
-        T hi = h[i] + omega * ((S + A) - h[i]);
-        T ho = h[i + 1] + omega * ((S - A) - h[i + 1]);
+        const T X = fma(m.rho, fma(mul_rn(T(4.5), cu), cu, -usq15), m.drho);  // S = w X
+        const T A = mul_rn(mul_rn(w, r3), cu);
+        T hi = fma(omega, add_rn(fma(w, X, A), -h[i]), h[i]);
+        T ho = fma(omega, add_rn(fma(w, X, -A), -h[i + 1]), h[i + 1]);
         if (forced) {
             const T cG = cdot<T>(i, m.Gx, m.Gy, m.Gz);
-            const T Fs = w * (T(9) * cu * cG - T(3) * uG), Fa = T(3) * w * cG;
-            hi += cf * (Fs + Fa);
-            ho += cf * (Fs - Fa);
+            const T Y = fma(mul_rn(T(9), cu), cG, mul_rn(T(-3), uG));  // Fs = w Y
+            const T Fa = mul_rn(mul_rn(T(3), w), cG);
+            hi = fma(cf, fma(w, Y, Fa), hi);
+            ho = fma(cf, fma(w, Y, -Fa), ho);
         }
         h[i] = hi;
         h[i + 1] = ho;
@@ -579,29 +560,30 @@ __device__ __forceinline__ void relax(T (&h)[Q], const Macro<T> &m, T omega, boo
 template <int Q, typename T>
 __device__ __forceinline__ void relax_trt(T (&h)[Q], const Macro<T> &m, T wp, T wm, bool forced)
 {
-    const T usq15 = T(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
-    const T cfp = T(1) - T(0.5) * wp, cfm = T(1) - T(0.5) * wm;
-    const T uG = m.ux * m.Gx + m.uy * m.Gy + m.uz * m.Gz;
+    const T usq15 = mul_rn(T(1.5), fma(m.uz, m.uz, fma(m.uy, m.uy, mul_rn(m.ux, m.ux))));
+    const T cfp = fma(T(-0.5), wp, T(1)), cfm = fma(T(-0.5), wm, T(1));
+    const T uG = fma(m.uz, m.Gz, fma(m.uy, m.Gy, mul_rn(m.ux, m.Gx)));
     {
         const T w0 = wgt<T>(Q, 0);
-        T h0 = h[0] - wp * (h[0] - w0 * (m.drho - m.rho * usq15));
-        if (forced) h0 += cfp * w0 * (T(-3) * uG);
+        T h0 = fma(-wp, fma(-w0, fma(-m.rho, usq15, m.drho), h[0]), h[0]);
+        if (forced) h0 = fma(mul_rn(cfp, w0), mul_rn(T(-3), uG), h0);
         h[0] = h0;
     }
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
         const T cu = cdot<T>(i, m.ux, m.uy, m.uz);
         const T w = wgt<T>(Q, i);
-        const T S = w * (m.drho + m.rho * (T(4.5) * cu * cu - usq15));
-        const T A = T(3) * w * m.rho * cu;
-        const T dp = wp * (T(0.5) * (h[i] + h[i + 1]) - S);
-        const T dm = wm * (T(0.5) * (h[i] - h[i + 1]) - A);
-        T hi = h[i] - dp - dm, ho = h[i + 1] - dp + dm;
+        const T X = fma(m.rho, fma(mul_rn(T(4.5), cu), cu, -usq15), m.drho);  // S = w X
+        const T A = mul_rn(mul_rn(mul_rn(T(3), w), m.rho), cu);
+        const T P = fma(-w, X, mul_rn(T(0.5), add_rn(h[i], h[i + 1])));  // even part minus S
+        const T M = fma(T(0.5), add_rn(h[i], -h[i + 1]), -A);           // odd part minus A
+        T hi = fma(-wm, M, fma(-wp, P, h[i])), ho = fma(wm, M, fma(-wp, P, h[i + 1]));
         if (forced) {
             const T cG = cdot<T>(i, m.Gx, m.Gy, m.Gz);
-            const T Fs = w * (T(9) * cu * cG - T(3) * uG), Fa = T(3) * w * cG;
-            hi += cfp * Fs + cfm * Fa;
-            ho += cfp * Fs - cfm * Fa;
+            const T Fs = mul_rn(w, fma(mul_rn(T(9), cu), cG, mul_rn(T(-3), uG)));
+            const T Fa = mul_rn(mul_rn(T(3), w), cG);
+            hi = fma(cfp, Fs, fma(cfm, Fa, hi));
+            ho = fma(cfp, Fs, fma(-cfm, Fa, ho));
         }
         h[i] = hi;
         h[i + 1] = ho;
@@ -610,7 +592,11 @@ __device__ __forceinline__ void relax_trt(T (&h)[Q], const Macro<T> &m, T wp, T 
 
 // Returns the density and velocity the collision used (mass and momentum
 // invariants of the new state).  Every step kernel collides with this
-// function, so the same pulled set gives the same bits in all of them.
+// function, so the same pulled set gives the same bits in all of them: the
+// collision's arithmetic (node_macros, pi_neq, relax, relax_trt and the
+// Smagorinsky time) spells out each rounding as fma, add_rn or mul_rn,
+// because ptxas may contract a plain multiply and add into an FMA in one
+// kernel and not in another.
 template <int Q, typename T, int CLOSURE>
 __device__ __forceinline__ Macro<T> collide_node(T (&h)[Q], bool forced, const KParams<T> &p)
 {
@@ -624,8 +610,10 @@ __device__ __forceinline__ Macro<T> collide_node(T (&h)[Q], bool forced, const K
     if (CLOSURE == LBM_CLOSURE_SMAGORINSKY) {
         T pi[6];
         pi_neq<Q, T>(h, m, pi);
-        const T pp = pi[0] * pi[0] + pi[1] * pi[1] + pi[2] * pi[2] + T(2) * (pi[3] * pi[3] + pi[4] * pi[4] + pi[5] * pi[5]);
-        const T te = T(0.5) * (p.tau + sqrt(p.tau * p.tau + p.smag18 * sqrt(T(2) * pp) * m.inv));
+        const T diag = fma(pi[2], pi[2], fma(pi[1], pi[1], mul_rn(pi[0], pi[0])));
+        const T offd = fma(pi[5], pi[5], fma(pi[4], pi[4], mul_rn(pi[3], pi[3])));
+        const T pp = fma(T(2), offd, diag);
+        const T te = mul_rn(T(0.5), add_rn(p.tau, sqrt(fma(p.tau, p.tau, mul_rn(mul_rn(p.smag18, sqrt(mul_rn(T(2), pp))), m.inv)))));
         omega = T(1) / te;
     }
     relax<Q, T>(h, m, omega, forced);
@@ -651,15 +639,22 @@ __device__ __forceinline__ void collide_stream_node(const S *__restrict__ A, S *
     unsigned t = 0;
     if (GENERAL) {
         t = tags[nb.self];
-        if (is_wall_tag(t & kTagMask)) return;
+        if (PAT == kPatAB && is_wall_tag(t & kTagMask)) return;
     }
 
     // Pull: h_i(x) = h*_i(x - c_i).  AA reads through B, the pointer the
     // launch writes, so same-address loads and stores keep program order.
+    // The AA steps issue the loads together with the tag's, before it is
+    // known whether the node is a wall (a wall node's AA sources are its own
+    // slots, which nothing else writes, and it discards what it read): on a
+    // 256^3 cavity 0.763 -> 0.788 of the roofline.  A/B keeps the early
+    // return, which measured faster there (0.828 against 0.770: loading
+    // first costs it 8 registers).
     const S *F = PAT == kPatAB ? A : B;
     T h[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) h[i] = pop_ld<S, PAT>(F + step_load_off<PAT>(i, g, nb));
+    if (GENERAL && PAT != kPatAB && is_wall_tag(t & kTagMask)) return;
     uint32_t wall = 0;
     if (GENERAL && (t & kNearWall)) wall = apply_walls<Q, S, PAT>(h, F, tags, g, nb, p);
 
@@ -783,7 +778,7 @@ __device__ __forceinline__ void compact_local_wall(T (&h)[Q], const int (&sv)[Q]
     const T rw = local_wall_rho<Q, T>(h, s);
 #pragma unroll
     for (int i = 1; i < Q; ++i)
-        if (sv[i] < -1) h[i] += rw * wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - sv[i]), p);
+        if (sv[i] < -1) h[i] = fma(rw, wall_term<Q, T>(i, (unsigned)(LBM_TAG_WALL0 - 2 - sv[i]), p), h[i]);
 }
 
 // The fused reduction's share of one node (FP32 compute): the density and
